@@ -1,0 +1,348 @@
+"""Benchmark: 3D complex FFT through the cyclic four-step method on one GB300.
+
+A step is one forward and one inverse transform of the 512^3 complex64
+workload (cyclic grid p = 8x8x8 by default) through the C ABI, i.e. one pass of
+the whole hot path in each direction.  Inputs (1 GiB) are larger than L2
+(129 MB), so no flush is needed between steps.  Metric: algorithmic HBM GB/s,
+B_alg = 4 * N * 8 bytes per transform (one round trip for phase A, one for
+phase B), divided by the measured time.
+
+Prints one JSON line (rank 0).  With --impl reference it times the FP64 CPU
+oracle instead (the reference arm of this single-GPU tier).
+Under torchrun with N > 1, every rank runs its own replica (no collective on
+the data path; the method's single all-to-all is not exercised on one node of
+replicas) and value is the sum over ranks at the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--shape", default="512,512,512")
+    ap.add_argument("--p", default="8,8,8")
+    ap.add_argument("--schedule", type=int, default=0, help="0 auto, 1 generic, 2 fused")
+    ap.add_argument("--seed", type=int, default=2024)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", default="512,512,512", help="oracle sample shape for cpu_baseline")
+    ap.add_argument("--ref-sample", default="256,256,256", help="oracle sample shape per reference step")
+    a = ap.parse_args()
+    a.warmup = max(3, a.warmup)
+    return a
+
+
+def shape_of(s):
+    return tuple(int(v) for v in s.split(","))
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def alg_bytes(shape, esize):
+    return 4 * math.prod(shape) * esize
+
+
+def oracle_cpu_run(shape, seed, reps=1):
+    """Time the FP64 oracle (forward + inverse) on a sample; returns (seconds per fwd+inv, cores)."""
+    import numpy as np
+    import oracle
+    from fftu_inputs import complex_uniform
+    x = complex_uniform(seed, shape, dtype=np.complex64).astype(np.complex128)
+    cores = oracle.max_threads()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        y = oracle.fftn(x)
+        oracle.fftn(y, inverse=True)
+    return (time.perf_counter() - t0) / reps, cores
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.out = os.path.join("/tmp", f"fftu_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            f = open(self.out, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu_index)], stdout=f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.out) as f:
+            for line in f:
+                parts = [v.strip() for v in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.out)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                "reasons": reasons}
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            table = json.load(f)
+        ent = table[kernel]
+        src = os.path.join(ROOT, ent["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if sha != ent["source_sha"]:
+            return None
+        return float(ent["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    shape = shape_of(args.shape)
+    sample = shape_of(args.ref_sample)
+    times, cores = [], None
+    for i in range(args.warmup + args.steps):
+        t, cores = oracle_cpu_run(sample, args.seed)
+        if i >= args.warmup:
+            times.append(t)
+    t = sum(times) / len(times)
+    value = 2 * alg_bytes(sample, 8) / t / 1e9
+    line = {
+        "metric": "3D FFT HBM GB/s (algorithmic bytes 4*N*8 per transform), forward+inverse",
+        "value": value, "unit": "GB/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{'x'.join(map(str, shape))} complex64 forward+inverse FFT",
+                   "shape": list(shape), "p": list(shape_of(args.p))},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": f"FP64 oracle forward+inverse of a {'x'.join(map(str, sample))} sample "
+                                   f"per step (seeded uniform inputs), GB/s scaled by the sample's 4*N*8 bytes"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2203_11795_gb300 import _build
+    _build.build()
+    import paper_2203_11795_gb300 as fftu
+    from fftu_inputs import complex_uniform
+
+    shape, p = shape_of(args.shape), shape_of(args.p)
+    N = math.prod(shape)
+    esize = 8
+    x_host = torch.from_numpy(complex_uniform(args.seed + rank, shape, dtype=np.complex64)).pin_memory()
+    x = x_host.to(dev)
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    fwd = fftu.Plan(shape, p, dtype=torch.complex64, schedule=args.schedule)
+    inv = fftu.Plan(shape, p, dtype=torch.complex64, inverse=True, schedule=args.schedule)
+    stream = torch.cuda.Stream(dev)
+    sh = stream.cuda_stream
+    A, B = fftu.FFTU_PHASE_A, fftu.FFTU_PHASE_B
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        fftu.fftu_exec_phase(fwd.handle, A, x.data_ptr(), y.data_ptr(), sh)
+        if ev is not None:
+            ev[1].record(stream)
+        fftu.fftu_exec_phase(fwd.handle, B, None, y.data_ptr(), sh)
+        if ev is not None:
+            ev[2].record(stream)
+        fftu.fftu_exec_phase(inv.handle, A, y.data_ptr(), z.data_ptr(), sh)
+        if ev is not None:
+            ev[3].record(stream)
+        fftu.fftu_exec_phase(inv.handle, B, None, z.data_ptr(), sh)
+        if ev is not None:
+            ev[4].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize(dev)
+
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    sampler = ClockSampler(local) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(events[k])
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop() if sampler else None
+    if world > 1:
+        dist.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    phase_a = [ev[0].elapsed_time(ev[1]) for ev in events] + [ev[2].elapsed_time(ev[3]) for ev in events]
+    phase_b = [ev[1].elapsed_time(ev[2]) for ev in events] + [ev[3].elapsed_time(ev[4]) for ev in events]
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+
+    # parity of the timed output (round trip) so a fast wrong kernel cannot pass unnoticed
+    rt_err = float((torch.linalg.vector_norm(z - x) / torch.linalg.vector_norm(x)).item())
+
+    e2e = None
+    if not args.no_e2e:
+        out_host = torch.empty_like(x_host).pin_memory()
+        xd = torch.empty_like(x)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for i in range(2 + args.e2e_steps):
+                if i == 2:
+                    torch.cuda.synchronize(dev)
+                    e0.record(stream)
+                xd.copy_(x_host, non_blocking=True)
+                fftu.fftu_exec(fwd.handle, xd.data_ptr(), y.data_ptr(), sh)
+                fftu.fftu_exec(inv.handle, y.data_ptr(), z.data_ptr(), sh)
+                out_host.copy_(z, non_blocking=True)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+        e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(e2e_t.item())
+        e2e = {"value": world * 2 * alg_bytes(shape, esize) / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": N * esize, "d2h_bytes_per_step": N * esize, "ms_per_step": e2e_ms,
+               "includes": "pinned H2D of the input, forward, inverse, D2H of the result"}
+
+    if rank == 0:
+        ms_per_step = total_ms / args.steps
+        value = world * 2 * alg_bytes(shape, esize) / (ms_per_step * 1e-3) / 1e9
+        peak, peak_kind = measured_peak()
+        ta, tb = statistics.mean(phase_a), statistics.mean(phase_b)
+        half = 2 * N * esize  # one HBM round trip: the algorithmic bytes of one phase
+        la, lb = fwd.info["launches_phase_a"], fwd.info["launches_phase_b"]
+        if ta >= tb:
+            dom, t_dom, launches = "phase_a", ta, la
+        else:
+            dom, t_dom, launches = "phase_b", tb, lb
+        kernel_name = f"{dom}_{'x'.join(map(str, shape))}_p{'x'.join(map(str, p))}"
+        achieved = half / (t_dom * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic_for(kernel_name), "kernel": dom, "launches_in_phase": launches,
+                    "peak_source": f"{peak_kind} hbm_gbs",
+                    "phase_ms": {"phase_a": ta, "phase_b": tb},
+                    "phase_frac": {"phase_a": half / (ta * 1e-3) / 1e9 / peak,
+                                   "phase_b": half / (tb * 1e-3) / 1e9 / peak}}
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            sample = shape_of(args.cpu_sample)
+            t_cpu, cores = oracle_cpu_run(sample, args.seed)
+            cpu = {"value": 2 * alg_bytes(sample, esize) / t_cpu / 1e9, "unit": "GB/s", "cores": cores,
+                   "kind": "oracle", "seconds": t_cpu,
+                   "sample": f"FP64 oracle forward+inverse of one {'x'.join(map(str, sample))} array "
+                             f"(same seeded inputs), GB/s scaled by 4*N*8 bytes per transform"}
+        line = {
+            "metric": "3D FFT HBM GB/s (algorithmic bytes 4*N*8 per transform), forward+inverse",
+            "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{'x'.join(map(str, shape))} complex64 forward+inverse FFT, cyclic "
+                                   f"p={'x'.join(map(str, p))}",
+                       "shape": list(shape), "p": list(p), "schedule": fwd.info["schedule"],
+                       "l2": "inputs (N*8 bytes) larger than L2 (129 MB); no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "gflops_5NlogN": world * 2 * 5 * N * math.log2(N) / (ms_per_step * 1e-3) / 1e9},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps * 2 * (la + lb),
+            "clocks": clocks,
+            "round_trip_rel_l2": rt_err,
+        }
+        print(json.dumps(line), flush=True)
+    fwd.close()
+    inv.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * fftu.h -- C ABI of the GB300 cyclic multidimensional FFT library (libfftu).
+ *
+ * The library computes the d-dimensional complex DFT
+ *     Y[k] = sum_j X[j] prod_l w_{n_l}^{j_l k_l},   w_n = exp(-2 pi i / n)
+ * (Koopman & Bisseling, "Minimizing communication in the multidimensional
+ * FFT", Sec. 1, eq. dftd) by the parallel four-step method of Algorithm 2.3
+ * (Sec. 2.2): the array is viewed as cyclically distributed over a virtual
+ * processor grid p_1 x ... x p_d (Sec. 1.1, phi(s, k) = s + k p); every
+ * virtual processor runs local strided sub-FFTs of shape n/p and a twiddle
+ * multiply (Superstep 0), the data are redistributed once (Superstep 1, the
+ * single all-to-all, realised on one GPU as the store pattern of the first
+ * phase), and the remaining length-p DFTs run in place (Superstep 2).  Input
+ * and output are in the same distribution, so on one GPU both are the plain
+ * row-major global array (Sec. 2.2, Algorithm 2.3 input/output).
+ *
+ * Everything in this header is plain C: no CUDA or C++ types cross it.
+ *
+ * Conventions for every entry point
+ *   - Arrays are row-major with the last axis contiguous (Sec. 3), n[0] is
+ *     the slowest axis.  Elements are interleaved (re, im) pairs: float for
+ *     FFTU_C64, double for FFTU_C128 (torch.complex64 / torch.complex128).
+ *   - Device pointers are CUDA device addresses on the device that was
+ *     current when the plan was made; they must be 16-byte aligned (float2 /
+ *     double2 access).  The caller owns them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Execution is stream-ordered and never synchronises the host.
+ *   - Errors are returned as fftu_status; no call aborts, traps or throws.
+ *     fftu_last_error() gives a one-line detail for the calling thread.
+ */
+#ifndef FFTU_H
+#define FFTU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FFTU_MAX_DIMS 8
+
+/* Opaque plan handle, owned by the library (fftu_destroy frees it). */
+typedef struct fftu_plan_st *fftu_handle;
+
+/* Element type: interleaved complex float (c64) or complex double (c128). */
+typedef enum { FFTU_C64 = 1, FFTU_C128 = 2 } fftu_dtype;
+
+/* Sign of the exponent.  FFTU_INVERSE conjugates every weight and scales the
+ * result by 1/N (Sec. 1.3: the same program with conjugated weights and the
+ * outcome scaled by 1/N). */
+typedef enum { FFTU_FORWARD = -1, FFTU_INVERSE = 1 } fftu_dir;
+
+typedef enum {
+    FFTU_OK = 0,
+    FFTU_ERR_ARG = 1,          /* null pointer, bad d, n_l < 1, p_l < 1, misalignment, wrong device */
+    FFTU_ERR_DIVISIBILITY = 2, /* p_l^2 does not divide n_l (Algorithm 2.3 input condition) */
+    FFTU_ERR_UNSUPPORTED = 3,  /* valid for the method but not for this GPU build (e.g. non power of two) */
+    FFTU_ERR_NOMEM = 4,        /* device allocation for tables or workspace failed */
+    FFTU_ERR_CUDA = 5,         /* a CUDA runtime call or kernel launch failed */
+    FFTU_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up (status word set by a kernel) */
+    FFTU_ERR_INTERNAL = 7      /* a device-side consistency check failed */
+} fftu_status;
+
+/* Which part of Algorithm 2.3 fftu_exec_phase runs. */
+typedef enum {
+    FFTU_PHASE_A = 1,  /* Superstep 0 + Superstep 1: local sub-FFTs, twiddle, redistribution */
+    FFTU_PHASE_B = 2,  /* Superstep 2: the length-p DFTs (and 1/N for the inverse), in place */
+    FFTU_PHASE_ALL = 3 /* both, i.e. the whole transform */
+} fftu_phase;
+
+/* Kernel schedule.  AUTO picks the fastest schedule the plan supports;
+ * GENERIC forces one strided pass per axis for each phase (any d, any
+ * power-of-two shape) and is kept as a cross-check of the fused kernels. */
+typedef enum { FFTU_SCHED_AUTO = 0, FFTU_SCHED_GENERIC = 1, FFTU_SCHED_FUSED = 2 } fftu_schedule;
+
+typedef struct {
+    int schedule;        /* fftu_schedule */
+    int reserved[7];     /* must be zero */
+} fftu_options;
+
+typedef struct {
+    int d;
+    int64_t n[FFTU_MAX_DIMS];
+    int64_t p[FFTU_MAX_DIMS];
+    int dtype;                 /* fftu_dtype */
+    int dir;                   /* fftu_dir */
+    int schedule;              /* schedule in use (fftu_schedule, never AUTO) */
+    int launches_phase_a;      /* kernel launches one phase A takes */
+    int launches_phase_b;      /* kernel launches one phase B takes */
+    int64_t N;                 /* number of elements */
+    int64_t alg_bytes;         /* algorithmic HBM bytes per transform: 4 * N * sizeof(element) */
+    int64_t table_bytes;       /* device bytes of twiddle tables owned by the plan */
+    int64_t workspace_bytes;   /* device bytes of workspace owned by the plan */
+} fftu_info;
+
+/*
+ * fftu_plan -- validate the problem and build a plan.
+ *   d        number of dimensions, 1 <= d <= FFTU_MAX_DIMS.
+ *   n[d]     array sizes, n[0] slowest; each n_l >= 1.  This GPU build
+ *            accepts powers of two only (else FFTU_ERR_UNSUPPORTED); the
+ *            method needs N "sufficiently composite" (Abstract).
+ *   p[d]     cyclic factors (virtual processor grid) with p_l^2 | n_l
+ *            (Algorithm 2.3 input; Sec. 2.3 gives the limit p_l <= sqrt(n_l)).
+ *            NULL lets the planner choose.
+ *   dtype    FFTU_C64 or FFTU_C128.
+ *   dir      FFTU_FORWARD or FFTU_INVERSE.
+ *   out      receives the handle; set to NULL on error.
+ * Allocates the plan's device tables (sum_l n_l entries of w_{n_l}^e,
+ * generated in FP64 on the device; cf. eq. weights) and any workspace, on the
+ * current device, and synchronises once.  Not stream-ordered.
+ */
+fftu_status fftu_plan(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,
+                      fftu_handle *out);
+
+/* fftu_plan with options (opts may be NULL = defaults). */
+fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,
+                         const fftu_options *opts, fftu_handle *out);
+
+/*
+ * fftu_exec -- run the whole transform (Algorithm 2.3) on `stream`.
+ *   in   device array of N elements (read only when in != out).
+ *   out  device array of N elements, receives V = DFT(X) in natural order.
+ *   in == out is allowed (in-place transform).  Other partial overlaps are
+ *   not allowed.  A plan may run on one stream at a time.
+ */
+fftu_status fftu_exec(fftu_handle plan, const void *in, void *out, void *stream);
+
+/*
+ * fftu_exec_phase -- run one part of Algorithm 2.3 (for staged checks).
+ *   FFTU_PHASE_A: in -> out.  out receives the redistributed data W in the
+ *                 global view: Z^{(s)}[m] (Superstep 0 output of virtual
+ *                 processor s at local index m) is stored at global index
+ *                 m + s (n/p), elementwise per axis (Superstep 1 Put).
+ *   FFTU_PHASE_B: in place on out (in must be NULL or equal to out): for every
+ *                 m in [n/p], the p values at m + s'(n/p) are replaced by
+ *                 their p_1 x ... x p_d DFT (Superstep 2), scaled by 1/N for
+ *                 the inverse.
+ *   FFTU_PHASE_ALL: same as fftu_exec.
+ */
+fftu_status fftu_exec_phase(fftu_handle plan, fftu_phase phase, const void *in, void *out,
+                            void *stream);
+
+/* Free the plan's device memory and the handle.  Synchronises the device
+ * with the plan's last use.  NULL is accepted. */
+fftu_status fftu_destroy(fftu_handle plan);
+
+/* Describe a plan (sizes, schedule, launches, byte counts). */
+fftu_status fftu_plan_info(fftu_handle plan, fftu_info *info);
+
+/* Read and clear the plan's device status word (bounded waits and device
+ * checks write it).  Synchronises with the plan's last use.  Returns FFTU_OK,
+ * FFTU_ERR_TIMEOUT or FFTU_ERR_INTERNAL. */
+fftu_status fftu_check_device_status(fftu_handle plan);
+
+/* Static string for a status code. */
+const char *fftu_status_string(fftu_status s);
+
+/* One-line detail about the last error on the calling thread ("" if none). */
+const char *fftu_last_error(void);
+
+/* Library version, e.g. "fftu 0.1.0 sm_103a". */
+const char *fftu_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFTU_H */

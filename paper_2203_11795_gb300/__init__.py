@@ -1,0 +1,216 @@
+"""Python binding of libfftu, the GB300 cyclic multidimensional FFT.
+
+Argument marshalling only: every step of the transform runs in the CUDA
+kernels of ``libfftu.so`` (built in-tree by ``_build.py``).  The functions
+below carry the C ABI's names (``include/fftu.h``) and take raw device
+pointers; ``Plan`` is a small convenience wrapper over torch tensors.  PyTorch
+supplies device memory and streams only.
+
+There is no CPU fallback: importing this package raises if the library has not
+been built, and every call raises ``FFTUError`` on a non-OK status.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfftu.so")
+
+FFTU_MAX_DIMS = 8
+FFTU_C64, FFTU_C128 = 1, 2
+FFTU_FORWARD, FFTU_INVERSE = -1, 1
+FFTU_PHASE_A, FFTU_PHASE_B, FFTU_PHASE_ALL = 1, 2, 3
+FFTU_SCHED_AUTO, FFTU_SCHED_GENERIC, FFTU_SCHED_FUSED = 0, 1, 2
+STATUS_NAMES = {0: "FFTU_OK", 1: "FFTU_ERR_ARG", 2: "FFTU_ERR_DIVISIBILITY", 3: "FFTU_ERR_UNSUPPORTED",
+                4: "FFTU_ERR_NOMEM", 5: "FFTU_ERR_CUDA", 6: "FFTU_ERR_TIMEOUT", 7: "FFTU_ERR_INTERNAL"}
+
+# Every entry point the header declares (checked by the test suite).
+EXPORTS = ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_destroy", "fftu_plan_info",
+           "fftu_check_device_status", "fftu_status_string", "fftu_last_error", "fftu_version")
+
+
+class FFTUError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        name = STATUS_NAMES.get(status, f"status {status}")
+        super().__init__(f"{where}: {name}" + (f" ({detail})" if detail else ""))
+
+
+class fftu_options(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class fftu_info(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("n", ctypes.c_int64 * FFTU_MAX_DIMS), ("p", ctypes.c_int64 * FFTU_MAX_DIMS),
+                ("dtype", ctypes.c_int), ("dir", ctypes.c_int), ("schedule", ctypes.c_int),
+                ("launches_phase_a", ctypes.c_int), ("launches_phase_b", ctypes.c_int),
+                ("N", ctypes.c_int64), ("alg_bytes", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_int64)]
+
+
+def _load_library() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libfftu.so is not built ({LIB_PATH}); run __graft_entry__.build() or "
+                          "python -m paper_2203_11795_gb300._build")
+    lib = ctypes.CDLL(LIB_PATH)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    vp = ctypes.c_void_p
+    h = ctypes.c_void_p
+    lib.fftu_plan.argtypes = [ctypes.c_int, i64p, i64p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(h)]
+    lib.fftu_plan_ex.argtypes = [ctypes.c_int, i64p, i64p, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(fftu_options), ctypes.POINTER(h)]
+    lib.fftu_exec.argtypes = [h, vp, vp, vp]
+    lib.fftu_exec_phase.argtypes = [h, ctypes.c_int, vp, vp, vp]
+    lib.fftu_destroy.argtypes = [h]
+    lib.fftu_plan_info.argtypes = [h, ctypes.POINTER(fftu_info)]
+    lib.fftu_check_device_status.argtypes = [h]
+    lib.fftu_status_string.argtypes = [ctypes.c_int]
+    lib.fftu_status_string.restype = ctypes.c_char_p
+    lib.fftu_last_error.restype = ctypes.c_char_p
+    lib.fftu_version.restype = ctypes.c_char_p
+    for name in ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_destroy",
+                 "fftu_plan_info", "fftu_check_device_status"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+_lib = _load_library()
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != 0:
+        raise FFTUError(rc, where, fftu_last_error())
+
+
+def _i64(vals):
+    if vals is None:
+        return None
+    return (ctypes.c_int64 * len(vals))(*[int(v) for v in vals])
+
+
+# ---- C ABI, same names -----------------------------------------------------------------
+
+def fftu_plan(d: int, n, p, dtype: int, direction: int) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.fftu_plan(int(d), _i64(n), _i64(p), int(dtype), int(direction), ctypes.byref(h)), "fftu_plan")
+    return h.value
+
+
+def fftu_plan_ex(d: int, n, p, dtype: int, direction: int, schedule: int = FFTU_SCHED_AUTO) -> int:
+    h = ctypes.c_void_p()
+    opts = fftu_options(schedule=int(schedule))
+    _check(_lib.fftu_plan_ex(int(d), _i64(n), _i64(p), int(dtype), int(direction), ctypes.byref(opts),
+                             ctypes.byref(h)), "fftu_plan_ex")
+    return h.value
+
+
+def fftu_exec(plan: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    _check(_lib.fftu_exec(plan, in_ptr, out_ptr, stream or None), "fftu_exec")
+
+
+def fftu_exec_phase(plan: int, phase: int, in_ptr, out_ptr: int, stream: int = 0) -> None:
+    _check(_lib.fftu_exec_phase(plan, int(phase), in_ptr, out_ptr, stream or None), "fftu_exec_phase")
+
+
+def fftu_destroy(plan: int) -> None:
+    _check(_lib.fftu_destroy(plan), "fftu_destroy")
+
+
+def fftu_plan_info(plan: int) -> dict:
+    info = fftu_info()
+    _check(_lib.fftu_plan_info(plan, ctypes.byref(info)), "fftu_plan_info")
+    d = info.d
+    return {"d": d, "n": list(info.n[:d]), "p": list(info.p[:d]), "dtype": info.dtype, "dir": info.dir,
+            "schedule": info.schedule, "launches_phase_a": info.launches_phase_a,
+            "launches_phase_b": info.launches_phase_b, "N": info.N, "alg_bytes": info.alg_bytes,
+            "table_bytes": info.table_bytes, "workspace_bytes": info.workspace_bytes}
+
+
+def fftu_check_device_status(plan: int) -> None:
+    _check(_lib.fftu_check_device_status(plan), "fftu_check_device_status")
+
+
+def fftu_status_string(status: int) -> str:
+    return _lib.fftu_status_string(int(status)).decode()
+
+
+def fftu_last_error() -> str:
+    return _lib.fftu_last_error().decode()
+
+
+def fftu_version() -> str:
+    return _lib.fftu_version().decode()
+
+
+# ---- torch convenience -----------------------------------------------------------------
+
+def _dtype_code(torch_dtype) -> int:
+    import torch
+    if torch_dtype == torch.complex64:
+        return FFTU_C64
+    if torch_dtype == torch.complex128:
+        return FFTU_C128
+    raise TypeError(f"unsupported dtype {torch_dtype}; use torch.complex64 or torch.complex128")
+
+
+class Plan:
+    """A plan for one shape, cyclic grid p, dtype and direction (fftu_plan)."""
+
+    def __init__(self, n, p=None, dtype=None, inverse: bool = False, schedule: int = FFTU_SCHED_AUTO):
+        import torch
+        self.n = tuple(int(v) for v in n)
+        self.dtype = dtype if dtype is not None else torch.complex64
+        code = _dtype_code(self.dtype)
+        self.inverse = bool(inverse)
+        self.handle = fftu_plan_ex(len(self.n), self.n, None if p is None else list(p), code,
+                                   FFTU_INVERSE if inverse else FFTU_FORWARD, schedule)
+        self.info = fftu_plan_info(self.handle)
+        self.p = tuple(self.info["p"])
+
+    def _validate(self, t, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != self.dtype or tuple(t.shape) != self.n or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {self.dtype} tensor of shape {self.n}")
+
+    def exec(self, x, out=None, stream=None):
+        """Whole transform; out defaults to a new tensor; out may be x (in place)."""
+        import torch
+        self._validate(x, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        self._validate(out, "out")
+        s = stream if stream is not None else torch.cuda.current_stream(x.device)
+        fftu_exec(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
+        return out
+
+    def exec_phase(self, phase: int, x, out, stream=None):
+        import torch
+        self._validate(out, "out")
+        if x is not None:
+            self._validate(x, "x")
+        s = stream if stream is not None else torch.cuda.current_stream(out.device)
+        fftu_exec_phase(self.handle, phase, None if x is None else x.data_ptr(), out.data_ptr(), s.cuda_stream)
+        return out
+
+    def check_device_status(self):
+        fftu_check_device_status(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fftu_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,217 @@
+// Generic strided sub-FFT pass along one axis, and the FP64 twiddle tables.
+//
+// One launch applies, to every line of one axis, a batch of independent
+// length-len DFTs on the strided classes of that line (see AxisPass in
+// fftu_internal.h).  Phase A of Algorithm 2.3 (Sec. 2.2) is one such pass per
+// axis in mode 0 (local sub-FFT F_{n_l/p_l} on the residue class s_l, the
+// twiddle w_{n_l}^{m_l s_l}, and the Put position m_l + s_l n_l/p_l of
+// Superstep 1); phase B is one pass per axis in mode 1 (F_{p_l} on the class
+// {m_l + s' n_l/p_l}, Superstep 2).  Applying the d-dim operators axis by axis
+// is exact because they are tensor products (Sec. 2.2, Y = (F_{n_1} x ... x F_{n_d}) X).
+//
+// Inside a tile the DFTs run as a self-sorting (Stockham) mixed-radix
+// sequence of radix-2/4/8/16 stages in shared memory: every thread reads its
+// butterflies' inputs into registers, the block synchronises, then writes the
+// outputs to their sorted positions.  Stage (radix R, span Ns) maps butterfly
+// b of a column to inputs b + r len/R, twiddles w_{Ns R}^{r (b mod Ns)}, and
+// outputs (b div Ns) Ns R + (b mod Ns) + r Ns.
+#include <cuda_runtime.h>
+
+#include "fft_device.cuh"
+#include "fftu_internal.h"
+
+namespace fftu {
+
+namespace {
+
+// complex values a thread holds per stage: 16 (c64) or 8 (c128)
+template <typename C> __host__ __device__ constexpr int ept() { return sizeof(C) == 8 ? kEptMax : kEptMax / 2; }
+constexpr int kAxisThreads = 512;
+
+template <typename C, int DIR, int R>
+__device__ __forceinline__ void stockham_stage(C *sm, const C *__restrict__ tw, const AxisPass &a, int Ns,
+                                               int tid, int nthreads) {
+    constexpr int B = ept<C>() / R > 0 ? ept<C>() / R : 1;  // butterflies per thread per stage
+    const int cols = a.G * a.V;
+    const int per_col = a.len / R;
+    const int total = cols * per_col;
+    const int twstep = a.nl / (Ns * R);
+    C v[B][R];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        const int w = tid + q * nthreads;
+        if (w < total) {
+            const int col = w % cols, b = w / cols;
+            int base, js;
+            if (a.contiguous) {
+                base = (col / a.G) * a.nl + (col % a.G);
+                js = a.G;
+            } else {
+                base = col;
+                js = cols;
+            }
+            const int k = b % Ns;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                C x = sm[base + (b + r * per_col) * js];
+                if (r > 0 && Ns > 1) x = cmul(x, dirw<DIR>(tw[r * k * twstep]));
+                v[q][r] = x;
+            }
+            dft_small<R, DIR>(v[q]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        const int w = tid + q * nthreads;
+        if (w < total) {
+            const int col = w % cols, b = w / cols;
+            int base, js;
+            if (a.contiguous) {
+                base = (col / a.G) * a.nl + (col % a.G);
+                js = a.G;
+            } else {
+                base = col;
+                js = cols;
+            }
+            const int k = b % Ns;
+            const int o = (b / Ns) * Ns * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm[base + (o + r * Ns) * js] = v[q][r];
+        }
+    }
+    __syncthreads();
+}
+
+// R0: radix of the first stage (1 = none); every later stage is radix 8.
+template <typename C, int DIR, int R0>
+__global__ void __launch_bounds__(kAxisThreads) axis_pass_kernel(const __grid_constant__ AxisPass a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    const C *__restrict__ src = static_cast<const C *>(a.src);
+    C *__restrict__ dst = static_cast<C *>(a.dst);
+    const C *__restrict__ tw = static_cast<const C *>(a.tw);
+    using Rl = typename real_of<C>::type;
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    for (int64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) {
+        int64_t gbase;
+        if (a.contiguous) {
+            gbase = t * (int64_t)a.V * a.nl;
+        } else {
+            const int64_t tpo = a.inner / a.V;
+            gbase = (t / tpo) * (int64_t)a.nl * a.inner + (t % tpo) * a.V;
+        }
+        // load: shared index e is the natural order of the tile
+        for (int e = tid; e < a.tile; e += nt) {
+            int64_t g = a.contiguous ? gbase + e : gbase + (int64_t)(e / a.V) * a.inner + (e % a.V);
+            sm[e] = src[g];
+        }
+        __syncthreads();
+
+        int Ns = 1;
+        if constexpr (R0 > 1) {
+            stockham_stage<C, DIR, R0>(sm, tw, a, Ns, tid, nt);
+            Ns = R0;
+        }
+        for (; Ns < a.len; Ns *= 8) stockham_stage<C, DIR, 8>(sm, tw, a, Ns, tid, nt);
+
+        // store with the output permutation, twiddle and scale
+        const Rl scale = (Rl)a.scale;
+        for (int e = tid; e < a.tile; e += nt) {
+            int lp, vv;  // output line position and vector
+            if (a.contiguous) {
+                vv = e / a.nl;
+                lp = e % a.nl;
+            } else {
+                lp = e / a.V;
+                vv = e % a.V;
+            }
+            C val;
+            if (a.mode == 0) {
+                const int c = lp / a.len, m = lp % a.len;
+                const int src_lp = c + m * a.G;
+                val = sm[a.contiguous ? vv * a.nl + src_lp : src_lp * a.V + vv];
+                if (c != 0 && m != 0) val = cmul(val, dirw<DIR>(tw[c * m]));
+            } else {
+                val = sm[e];
+            }
+            if (a.scale != 1.0) val = cscale(val, scale);
+            int64_t g = a.contiguous ? gbase + e : gbase + (int64_t)lp * a.inner + vv;
+            dst[g] = val;
+        }
+        __syncthreads();
+    }
+}
+
+// w_n^e = exp(-2 pi i e / n) for e in [n], evaluated in FP64 by sincospi on the
+// exactly reduced exponent, then rounded once to the table's precision.
+template <typename C>
+__global__ void twiddle_table_kernel(C *dst, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * (double)e / (double)n, &s, &c);
+        C w;
+        w.x = (typename real_of<C>::type)c;
+        w.y = (typename real_of<C>::type)s;
+        dst[e] = w;
+    }
+}
+
+template <typename C, int DIR>
+cudaError_t launch_axis_t(const AxisPass &a, cudaStream_t st) {
+    size_t smem = (size_t)a.tile * sizeof(C);
+    int64_t grid = a.tiles < (int64_t)1 << 30 ? a.tiles : (int64_t)1 << 30;
+    const int r0 = a.nstages > 0 && a.radix[0] != 8 ? a.radix[0] : 1;
+    switch (r0) {
+        case 2: axis_pass_kernel<C, DIR, 2><<<(unsigned)grid, a.threads, smem, st>>>(a); break;
+        case 4: axis_pass_kernel<C, DIR, 4><<<(unsigned)grid, a.threads, smem, st>>>(a); break;
+        case 16: axis_pass_kernel<C, DIR, 16><<<(unsigned)grid, a.threads, smem, st>>>(a); break;
+        default: axis_pass_kernel<C, DIR, 1><<<(unsigned)grid, a.threads, smem, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename C, int DIR, int R0>
+cudaError_t prepare_axis_r() {
+    return cudaFuncSetAttribute(axis_pass_kernel<C, DIR, R0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kMaxDynSmem);
+}
+
+template <typename C, int DIR>
+cudaError_t prepare_axis_t() {
+    cudaError_t e = prepare_axis_r<C, DIR, 1>();
+    if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 2>();
+    if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 4>();
+    if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 16>();
+    return e;
+}
+
+}  // namespace
+
+size_t axis_pass_smem_bytes(const AxisPass &a, int is_double) {
+    return (size_t)a.tile * (is_double ? sizeof(double2) : sizeof(float2));
+}
+
+cudaError_t launch_axis_pass(const AxisPass &a, int is_double, int dir, cudaStream_t st) {
+    if (is_double) return dir < 0 ? launch_axis_t<double2, -1>(a, st) : launch_axis_t<double2, 1>(a, st);
+    return dir < 0 ? launch_axis_t<float2, -1>(a, st) : launch_axis_t<float2, 1>(a, st);
+}
+
+cudaError_t prepare_axis_pass(int is_double, int dir) {
+    if (is_double) return dir < 0 ? prepare_axis_t<double2, -1>() : prepare_axis_t<double2, 1>();
+    return dir < 0 ? prepare_axis_t<float2, -1>() : prepare_axis_t<float2, 1>();
+}
+
+cudaError_t launch_twiddle_table(void *dst, int64_t n, int is_double, cudaStream_t st) {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    if (is_double)
+        twiddle_table_kernel<double2><<<(unsigned)blocks, 256, 0, st>>>(static_cast<double2 *>(dst), n);
+    else
+        twiddle_table_kernel<float2><<<(unsigned)blocks, 256, 0, st>>>(static_cast<float2 *>(dst), n);
+    return cudaGetLastError();
+}
+
+}  // namespace fftu

@@ -1,0 +1,526 @@
+// C ABI of libfftu: validation, planning, and stream-ordered execution of
+// Algorithm 2.3 (Sec. 2.2) on one GPU.
+//
+// A plan is a list of kernel launches for phase A (Superstep 0 + the
+// Superstep 1 redistribution, realised by the store positions) and for phase B
+// (Superstep 2, in place).  The plan owns the FP64-generated twiddle tables
+// (one table of w_{n_l}^e, e in [n_l], per axis: sum_l n_l entries; the
+// paper's per-processor table of eq. weights holds the n_l/p_l entries one
+// processor needs, here every virtual processor reads the shared table) and a
+// device status word.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fftu_internal.h"
+
+namespace fftu {
+
+namespace {
+
+thread_local char g_err[320] = "";
+
+void set_err(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+fftu_status cuda_fail(cudaError_t e, const char *what) {
+    set_err("%s: %s", what, cudaGetErrorString(e));
+    return FFTU_ERR_CUDA;
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int ilog2(int64_t v) {
+    int r = 0;
+    while ((int64_t(1) << r) < v) ++r;
+    return r;
+}
+
+// Radix sequence for a power-of-two length: radix 8 where possible, a single
+// 16 or 4 to absorb the remainder, radix 2 only for length 2.
+int radix_plan(int len, int *radix) {
+    int k = ilog2(len), n = 0;
+    if (k == 0) return 0;
+    int eights = k / 3, rem = k % 3;
+    if (rem == 1) {
+        if (eights >= 1) {
+            radix[n++] = 16;
+            --eights;
+        } else {
+            radix[n++] = 2;
+        }
+    } else if (rem == 2) {
+        radix[n++] = 4;
+    }
+    for (int i = 0; i < eights; ++i) radix[n++] = 8;
+    return n;
+}
+
+enum StepKind { STEP_AXIS = 1, STEP_PHASE_B_FUSED = 2 };
+
+struct Step {
+    int kind;
+    AxisPass axis;
+    PhaseBFused pb;
+};
+
+}  // namespace
+
+struct Plan {
+    int d = 0;
+    int64_t n[FFTU_MAX_DIMS] = {};
+    int64_t p[FFTU_MAX_DIMS] = {};
+    int dtype = 0, dir = 0, device = 0, schedule = 0;
+    int64_t N = 0;
+    size_t esize = 0;
+    void *tables = nullptr;
+    size_t table_bytes = 0;
+    int64_t table_off[FFTU_MAX_DIMS] = {};
+    void *workspace = nullptr;
+    size_t workspace_bytes = 0;
+    int *dstatus = nullptr;
+    std::vector<Step> phase_a, phase_b;
+
+    const void *table(int l) const { return static_cast<const char *>(tables) + table_off[l] * esize; }
+};
+
+namespace {
+
+// Generic schedule: one strided pass per axis.  mode 0 = phase A, mode 1 = phase B.
+fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPass &a) {
+    std::memset(&a, 0, sizeof(a));
+    const int is_double = pl.dtype == FFTU_C128;
+    int64_t outer = 1, inner = 1;
+    for (int k = 0; k < l; ++k) outer *= pl.n[k];
+    for (int k = l + 1; k < pl.d; ++k) inner *= pl.n[k];
+    const int64_t nl = pl.n[l], Ll = pl.n[l] / pl.p[l];
+    const int64_t target = is_double ? 4096 : 8192;
+    const int64_t maxtile = is_double ? kMaxGenericTile / 4 : kMaxGenericTile / 2;
+    if (nl > maxtile) {
+        set_err("axis %d: length %lld exceeds the generic pass tile limit %lld", l, (long long)nl,
+                (long long)maxtile);
+        return FFTU_ERR_UNSUPPORTED;
+    }
+    a.outer = outer;
+    a.inner = inner;
+    a.nl = (int)nl;
+    if (mode == 0) {
+        a.len = (int)Ll;
+        a.G = (int)pl.p[l];
+    } else {
+        a.len = (int)pl.p[l];
+        a.G = (int)Ll;
+    }
+    a.mode = mode;
+    a.contiguous = inner == 1;
+    int64_t V = target / nl;
+    if (V < 1) V = 1;
+    const int64_t cap = a.contiguous ? outer : inner;
+    if (V > cap) V = cap;
+    a.V = (int)V;
+    a.tile = (int)(nl * V);
+    a.tiles = a.contiguous ? outer / V : outer * (inner / V);
+    const int ept = is_double ? kEptMax / 2 : kEptMax;
+    int th = (a.tile + ept - 1) / ept;
+    th = ((th + 31) / 32) * 32;
+    if (th < 32) th = 32;
+    if (th > 512) th = 512;
+    a.threads = th;
+    a.tw = pl.table(l);
+    a.scale = scale;
+    a.nstages = radix_plan(a.len, a.radix);
+    return FFTU_OK;
+}
+
+bool make_phase_b_fused(const Plan &pl, double scale, PhaseBFused &b) {
+    std::memset(&b, 0, sizeof(b));
+    const size_t es = pl.esize;
+    int P = 1;
+    for (int l = 0; l < pl.d; ++l) {
+        if (pl.p[l] > 16) return false;
+        P *= (int)pl.p[l];
+    }
+    b.data = nullptr;
+    b.d = pl.d;
+    int64_t stride = 1;
+    for (int l = pl.d - 1; l >= 0; --l) {
+        b.n[l] = pl.n[l];
+        b.p[l] = (int)pl.p[l];
+        b.L[l] = pl.n[l] / pl.p[l];
+        b.stride[l] = stride;
+        stride *= pl.n[l];
+    }
+    b.P = P;
+    const size_t budget = 64 * 1024;
+    int64_t Mt = b.L[pl.d - 1];
+    while (Mt > 1 && (size_t)P * Mt * es > budget) Mt /= 2;
+    if ((size_t)P * Mt * es > (size_t)kMaxDynSmem) return false;
+    b.Mt = (int)Mt;
+    int64_t groups = 1;
+    for (int l = 0; l < pl.d - 1; ++l) groups *= b.L[l];
+    b.tiles = groups * (b.L[pl.d - 1] / Mt);
+    b.threads = 256;
+    b.scale = scale;
+    return true;
+}
+
+fftu_status build_schedule(Plan &pl, int sched) {
+    const double scale = pl.dir == FFTU_INVERSE ? 1.0 / (double)pl.N : 1.0;
+    // Phase A: contiguous axis first (reads the caller's array in long runs).
+    for (int l = pl.d - 1; l >= 0; --l) {
+        if (pl.n[l] == 1) continue;
+        Step s;
+        s.kind = STEP_AXIS;
+        fftu_status st = make_axis_pass(pl, l, 0, 1.0, s.axis);
+        if (st != FFTU_OK) return st;
+        pl.phase_a.push_back(s);
+    }
+    // Phase B: one fused pass when every p_l <= 16, else one pass per axis.
+    Step s;
+    if (sched != FFTU_SCHED_GENERIC && make_phase_b_fused(pl, scale, s.pb)) {
+        s.kind = STEP_PHASE_B_FUSED;
+        pl.phase_b.push_back(s);
+    } else {
+        int last = -1;
+        for (int l = 0; l < pl.d; ++l)
+            if (pl.p[l] > 1) last = l;
+        if (last < 0) last = pl.d - 1;  // every p_l = 1: a single pass applies the scale
+        for (int l = pl.d - 1; l >= 0; --l) {
+            if (pl.p[l] == 1 && l != last) continue;
+            Step t;
+            t.kind = STEP_AXIS;
+            fftu_status st = make_axis_pass(pl, l, 1, l == last ? scale : 1.0, t.axis);
+            if (st != FFTU_OK) return st;
+            pl.phase_b.push_back(t);
+        }
+    }
+    pl.schedule = sched == FFTU_SCHED_GENERIC ? FFTU_SCHED_GENERIC : FFTU_SCHED_FUSED;
+    return FFTU_OK;
+}
+
+void free_plan(Plan *pl) {
+    if (!pl) return;
+    if (pl->tables) cudaFree(pl->tables);
+    if (pl->workspace) cudaFree(pl->workspace);
+    if (pl->dstatus) cudaFree(pl->dstatus);
+    delete pl;
+}
+
+fftu_status run_steps(Plan *pl, const std::vector<Step> &steps, const void *first_src, void *dst,
+                      cudaStream_t st) {
+    const int is_double = pl->dtype == FFTU_C128;
+    const void *src = first_src;
+    if (steps.empty() && src != dst) {  // N = 1 or all n_l = 1: the transform is the identity
+        cudaError_t e = cudaMemcpyAsync(dst, src, (size_t)pl->N * pl->esize, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "copy");
+    }
+    for (const Step &s : steps) {
+        cudaError_t e;
+        if (s.kind == STEP_AXIS) {
+            AxisPass a = s.axis;
+            a.src = src;
+            a.dst = dst;
+            e = launch_axis_pass(a, is_double, pl->dir, st);
+        } else {
+            PhaseBFused b = s.pb;
+            b.data = dst;
+            e = launch_phase_b_fused(b, is_double, pl->dir, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        src = dst;
+    }
+    return FFTU_OK;
+}
+
+}  // namespace
+
+}  // namespace fftu
+
+using fftu::Plan;
+
+struct fftu_plan_st {
+    Plan *impl;
+};
+
+extern "C" {
+
+fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,
+                         const fftu_options *opts, fftu_handle *out) {
+    using namespace fftu;
+    g_err[0] = '\0';
+    if (!out) {
+        set_err("out is NULL");
+        return FFTU_ERR_ARG;
+    }
+    *out = nullptr;
+    if (d < 1 || d > FFTU_MAX_DIMS || !n) {
+        set_err("d must be in [1, %d] and n non-NULL", FFTU_MAX_DIMS);
+        return FFTU_ERR_ARG;
+    }
+    if (dtype != FFTU_C64 && dtype != FFTU_C128) {
+        set_err("dtype must be FFTU_C64 or FFTU_C128");
+        return FFTU_ERR_ARG;
+    }
+    if (dir != FFTU_FORWARD && dir != FFTU_INVERSE) {
+        set_err("dir must be FFTU_FORWARD or FFTU_INVERSE");
+        return FFTU_ERR_ARG;
+    }
+    int sched = opts ? opts->schedule : FFTU_SCHED_AUTO;
+    if (sched < FFTU_SCHED_AUTO || sched > FFTU_SCHED_FUSED) {
+        set_err("unknown schedule %d", sched);
+        return FFTU_ERR_ARG;
+    }
+    if (opts)
+        for (int r : opts->reserved)
+            if (r != 0) {
+                set_err("fftu_options.reserved must be zero");
+                return FFTU_ERR_ARG;
+            }
+    int64_t N = 1;
+    int64_t pp[FFTU_MAX_DIMS];
+    for (int l = 0; l < d; ++l) {
+        if (n[l] < 1) {
+            set_err("n[%d] = %lld < 1", l, (long long)n[l]);
+            return FFTU_ERR_ARG;
+        }
+        if (n[l] > (int64_t(1) << 40) || N > (int64_t(1) << 40) / n[l]) {
+            set_err("N exceeds 2^40 elements");
+            return FFTU_ERR_ARG;
+        }
+        N *= n[l];
+        if (p) {
+            if (p[l] < 1) {
+                set_err("p[%d] = %lld < 1", l, (long long)p[l]);
+                return FFTU_ERR_ARG;
+            }
+            if (n[l] % (p[l] * p[l]) != 0) {
+                set_err("p[%d]^2 = %lld does not divide n[%d] = %lld", l, (long long)(p[l] * p[l]), l,
+                        (long long)n[l]);
+                return FFTU_ERR_DIVISIBILITY;
+            }
+            pp[l] = p[l];
+        } else {
+            // default grid: the largest power of two with p_l^2 | n_l, at most 8
+            int64_t q = 1;
+            while (q < 8 && n[l] % ((2 * q) * (2 * q)) == 0) q *= 2;
+            pp[l] = q;
+        }
+    }
+    for (int l = 0; l < d; ++l)
+        if (!is_pow2(n[l])) {
+            set_err("n[%d] = %lld is not a power of two (GPU build supports powers of two)", l, (long long)n[l]);
+            return FFTU_ERR_UNSUPPORTED;
+        }
+
+    Plan *pl = new (std::nothrow) Plan();
+    if (!pl) {
+        set_err("host allocation failed");
+        return FFTU_ERR_NOMEM;
+    }
+    pl->d = d;
+    for (int l = 0; l < d; ++l) {
+        pl->n[l] = n[l];
+        pl->p[l] = pp[l];
+    }
+    pl->dtype = dtype;
+    pl->dir = dir;
+    pl->N = N;
+    pl->esize = dtype == FFTU_C128 ? 16 : 8;
+    cudaError_t e = cudaGetDevice(&pl->device);
+    if (e != cudaSuccess) {
+        free_plan(pl);
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    // twiddle tables
+    int64_t off = 0;
+    for (int l = 0; l < d; ++l) {
+        pl->table_off[l] = off;
+        off += n[l];
+    }
+    pl->table_bytes = (size_t)off * pl->esize;
+    e = cudaMalloc(&pl->tables, pl->table_bytes);
+    if (e != cudaSuccess) {
+        free_plan(pl);
+        set_err("cudaMalloc of %zu table bytes: %s", pl->table_bytes, cudaGetErrorString(e));
+        cudaGetLastError();
+        return FFTU_ERR_NOMEM;
+    }
+    e = cudaMalloc(&pl->dstatus, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(pl->dstatus, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        free_plan(pl);
+        cudaGetLastError();
+        set_err("status word allocation: %s", cudaGetErrorString(e));
+        return FFTU_ERR_NOMEM;
+    }
+    for (int l = 0; l < d && e == cudaSuccess; ++l)
+        e = launch_twiddle_table(static_cast<char *>(pl->tables) + pl->table_off[l] * pl->esize, n[l],
+                                 dtype == FFTU_C128, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_plan(pl);
+        return cuda_fail(e, "twiddle table generation");
+    }
+    e = prepare_axis_pass(dtype == FFTU_C128, dir);
+    if (e == cudaSuccess) e = prepare_phase_b_fused(dtype == FFTU_C128, dir);
+    if (e != cudaSuccess) {
+        free_plan(pl);
+        return cuda_fail(e, "kernel attributes");
+    }
+    fftu_status st = build_schedule(*pl, sched);
+    if (st != FFTU_OK) {
+        free_plan(pl);
+        return st;
+    }
+    fftu_plan_st *h = new (std::nothrow) fftu_plan_st;
+    if (!h) {
+        free_plan(pl);
+        set_err("host allocation failed");
+        return FFTU_ERR_NOMEM;
+    }
+    h->impl = pl;
+    *out = h;
+    return FFTU_OK;
+}
+
+fftu_status fftu_plan(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,
+                      fftu_handle *out) {
+    return fftu_plan_ex(d, n, p, dtype, dir, nullptr, out);
+}
+
+fftu_status fftu_exec_phase(fftu_handle h, fftu_phase phase, const void *in, void *out, void *stream) {
+    using namespace fftu;
+    g_err[0] = '\0';
+    if (!h || !h->impl) {
+        set_err("plan is NULL");
+        return FFTU_ERR_ARG;
+    }
+    Plan *pl = h->impl;
+    if (phase != FFTU_PHASE_A && phase != FFTU_PHASE_B && phase != FFTU_PHASE_ALL) {
+        set_err("unknown phase %d", (int)phase);
+        return FFTU_ERR_ARG;
+    }
+    if (!out || ((phase & FFTU_PHASE_A) && !in)) {
+        set_err("in/out must be non-NULL device pointers");
+        return FFTU_ERR_ARG;
+    }
+    if (phase == FFTU_PHASE_B && in && in != out) {
+        set_err("phase B runs in place: in must be NULL or equal to out");
+        return FFTU_ERR_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) {
+        set_err("in/out must be 16-byte aligned");
+        return FFTU_ERR_ARG;
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != pl->device) {
+        set_err("plan was made on device %d, current device is %d", pl->device, dev);
+        return FFTU_ERR_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (phase & FFTU_PHASE_A) {
+        fftu_status s = run_steps(pl, pl->phase_a, in, out, st);
+        if (s != FFTU_OK) return s;
+    }
+    if (phase & FFTU_PHASE_B) {
+        fftu_status s = run_steps(pl, pl->phase_b, out, out, st);
+        if (s != FFTU_OK) return s;
+    }
+    return FFTU_OK;
+}
+
+fftu_status fftu_exec(fftu_handle h, const void *in, void *out, void *stream) {
+    return fftu_exec_phase(h, FFTU_PHASE_ALL, in, out, stream);
+}
+
+fftu_status fftu_destroy(fftu_handle h) {
+    using namespace fftu;
+    g_err[0] = '\0';
+    if (!h) return FFTU_OK;
+    Plan *pl = h->impl;
+    fftu_status rc = FFTU_OK;
+    if (pl) {
+        int prev = -1;
+        const int dev = pl->device;
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = cuda_fail(e, "synchronize before destroy");
+        free_plan(pl);
+        if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    }
+    delete h;
+    return rc;
+}
+
+fftu_status fftu_plan_info(fftu_handle h, fftu_info *info) {
+    using namespace fftu;
+    if (!h || !h->impl || !info) {
+        set_err("plan and info must be non-NULL");
+        return FFTU_ERR_ARG;
+    }
+    const Plan *pl = h->impl;
+    std::memset(info, 0, sizeof(*info));
+    info->d = pl->d;
+    for (int l = 0; l < pl->d; ++l) {
+        info->n[l] = pl->n[l];
+        info->p[l] = pl->p[l];
+    }
+    info->dtype = pl->dtype;
+    info->dir = pl->dir;
+    info->schedule = pl->schedule;
+    info->launches_phase_a = (int)pl->phase_a.size();
+    info->launches_phase_b = (int)pl->phase_b.size();
+    info->N = pl->N;
+    info->alg_bytes = 4 * pl->N * (int64_t)pl->esize;
+    info->table_bytes = (int64_t)pl->table_bytes;
+    info->workspace_bytes = (int64_t)pl->workspace_bytes;
+    return FFTU_OK;
+}
+
+fftu_status fftu_check_device_status(fftu_handle h) {
+    using namespace fftu;
+    if (!h || !h->impl) {
+        set_err("plan is NULL");
+        return FFTU_ERR_ARG;
+    }
+    Plan *pl = h->impl;
+    int v = 0;
+    cudaError_t e = cudaMemcpy(&v, pl->dstatus, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(pl->dstatus, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "status word read");
+    if (v == 0) return FFTU_OK;
+    set_err("device status word = %d", v);
+    return v == FFTU_ERR_TIMEOUT ? FFTU_ERR_TIMEOUT : FFTU_ERR_INTERNAL;
+}
+
+const char *fftu_status_string(fftu_status s) {
+    switch (s) {
+        case FFTU_OK: return "FFTU_OK";
+        case FFTU_ERR_ARG: return "FFTU_ERR_ARG: invalid argument";
+        case FFTU_ERR_DIVISIBILITY: return "FFTU_ERR_DIVISIBILITY: p_l^2 must divide n_l";
+        case FFTU_ERR_UNSUPPORTED: return "FFTU_ERR_UNSUPPORTED: not supported by this GPU build";
+        case FFTU_ERR_NOMEM: return "FFTU_ERR_NOMEM: device allocation failed";
+        case FFTU_ERR_CUDA: return "FFTU_ERR_CUDA: CUDA runtime error";
+        case FFTU_ERR_TIMEOUT: return "FFTU_ERR_TIMEOUT: bounded device wait expired";
+        case FFTU_ERR_INTERNAL: return "FFTU_ERR_INTERNAL: device consistency check failed";
+    }
+    return "FFTU status: unknown code";
+}
+
+const char *fftu_last_error(void) { return fftu::g_err; }
+
+const char *fftu_version(void) { return "fftu 0.1.0 sm_103a"; }
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fftu.h"
+
+namespace fftu {
+
+constexpr int kMaxStages = 24;
+constexpr int kEptMax = 16;            // complex values a thread holds per stage of the generic pass
+constexpr int kMaxGenericTile = 16384; // elements per tile of the generic pass (kEptMax * 1024 threads)
+constexpr int kMaxDynSmem = 200 * 1024; // dynamic shared memory ceiling requested for any kernel
+
+// One strided sub-FFT pass along one axis (generic schedule).
+//
+// The array is viewed as [outer][nl][inner].  A line (fixed outer, inner) of
+// nl = len * G elements splits into G classes; class c holds the elements at
+// line positions c + j G, j in [len].  Each class gets a length-len DFT.
+//   mode 0 (phase A, Superstep 0 + Put): class c = residue s of the cyclic
+//     distribution (G = p_l, len = n_l/p_l); output m is multiplied by the
+//     twiddle w_{n_l}^{m s} and stored at line position s len + m.
+//   mode 1 (phase B, Superstep 2): class c = local index m (G = n_l/p_l,
+//     len = p_l); output k is stored in place at c + k G, times `scale`.
+struct AxisPass {
+    const void *src;
+    void *dst;
+    int64_t outer, inner;
+    int nl, len, G;
+    int mode;
+    int V;            // vectors per tile: inner indices (strided axis) or lines (contiguous axis)
+    int contiguous;   // inner == 1
+    int tile;         // nl * V
+    int threads;
+    const void *tw;   // w_{nl}^e, e in [nl] (forward roots)
+    double scale;
+    int nstages;
+    int radix[kMaxStages];
+    int64_t tiles;
+};
+
+// Phase B on the d-dim groups {m + s' (n/p)} with every p_l <= 16, in one pass.
+// Tile = all p values for Mt consecutive m along the last axis.
+struct PhaseBFused {
+    void *data;
+    int d;
+    int64_t n[FFTU_MAX_DIMS];
+    int64_t L[FFTU_MAX_DIMS];      // n_l / p_l
+    int p[FFTU_MAX_DIMS];
+    int64_t stride[FFTU_MAX_DIMS]; // element stride of axis l in the global array
+    int P;                         // prod p_l
+    int Mt;                        // consecutive m_d per tile
+    int64_t tiles;
+    int threads;
+    double scale;
+};
+
+struct Plan;
+
+// Kernel launchers (return cudaGetLastError() of the launch).
+// Set per-device kernel attributes (dynamic shared memory); called at plan time.
+cudaError_t prepare_axis_pass(int is_double, int dir);
+cudaError_t prepare_phase_b_fused(int is_double, int dir);
+cudaError_t launch_twiddle_table(void *dst, int64_t n, int is_double, cudaStream_t st);
+cudaError_t launch_axis_pass(const AxisPass &a, int is_double, int dir, cudaStream_t st);
+cudaError_t launch_phase_b_fused(const PhaseBFused &b, int is_double, int dir, cudaStream_t st);
+size_t axis_pass_smem_bytes(const AxisPass &a, int is_double);
+size_t phase_b_fused_smem_bytes(const PhaseBFused &b, int is_double);
+
+}  // namespace fftu

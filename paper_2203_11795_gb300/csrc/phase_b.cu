@@ -1,0 +1,130 @@
+// Phase B in one pass: Superstep 2 of Algorithm 2.3 (Sec. 2.2) when every
+// p_l <= 16.
+//
+// After the redistribution, the p = p_1 ... p_d values that one length-p DFT
+// needs sit at the global positions m + s' (n/p), s' in [p_1] x ... x [p_d],
+// for a fixed m in [n/p] (per axis m_l + s'_l n_l/p_l; Superstep 2 applies
+// F_{p_1} x ... x F_{p_d} to W^{(s)}(t : n/p^2 : n/p), whose global positions
+// are exactly these).  The output k is written back to m + k (n/p), so the
+// pass is in place.
+//
+// A tile holds all p values for Mt consecutive m_d (the contiguous axis), so
+// every global access is a run of Mt elements.  The DFT along axis l is one
+// radix-p_l butterfly per group, in shared memory; axes are separated by block
+// barriers.  The inverse multiplies by 1/N in the store.
+#include <cuda_runtime.h>
+
+#include "fft_device.cuh"
+#include "fftu_internal.h"
+
+namespace fftu {
+
+namespace {
+
+template <typename C, int DIR, int R>
+__device__ __forceinline__ void axis_dft(C *sm, int total, int S, int tid, int nt) {
+    // groups: total / R, group g -> base (g / S) * S * R + g % S, stride S
+    const int groups = total / R;
+    for (int g = tid; g < groups; g += nt) {
+        const int base = (g / S) * S * R + (g % S);
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = sm[base + r * S];
+        dft_small<R, DIR>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[base + r * S] = v[r];
+    }
+}
+
+template <typename C, int DIR>
+__global__ void __launch_bounds__(256) phase_b_fused_kernel(const __grid_constant__ PhaseBFused b) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    C *__restrict__ data = static_cast<C *>(b.data);
+    using Rl = typename real_of<C>::type;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int d = b.d;
+    const int total = b.P * b.Mt;
+    const int64_t tiles_d = b.L[d - 1] / b.Mt;
+
+    for (int64_t t = blockIdx.x; t < b.tiles; t += gridDim.x) {
+        // tile -> fixed m_0..m_{d-2} and the first m_{d-1}
+        int64_t rem = t / tiles_d;
+        int64_t base = (t % tiles_d) * b.Mt * b.stride[d - 1];
+        for (int l = d - 2; l >= 0; --l) {
+            base += (rem % b.L[l]) * b.stride[l];
+            rem /= b.L[l];
+        }
+        for (int e = tid; e < total; e += nt) {
+            const int mt = e % b.Mt;
+            int sf = e / b.Mt;
+            int64_t g = base + (int64_t)mt * b.stride[d - 1];
+            for (int l = d - 1; l >= 0; --l) {
+                const int sl = sf % b.p[l];
+                sf /= b.p[l];
+                g += (int64_t)sl * b.L[l] * b.stride[l];
+            }
+            sm[e] = data[g];
+        }
+        __syncthreads();
+        int S = b.Mt;
+        for (int l = d - 1; l >= 0; --l) {
+            switch (b.p[l]) {
+                case 2: axis_dft<C, DIR, 2>(sm, total, S, tid, nt); break;
+                case 4: axis_dft<C, DIR, 4>(sm, total, S, tid, nt); break;
+                case 8: axis_dft<C, DIR, 8>(sm, total, S, tid, nt); break;
+                case 16: axis_dft<C, DIR, 16>(sm, total, S, tid, nt); break;
+                default: break;
+            }
+            S *= b.p[l];
+            __syncthreads();
+        }
+        const Rl scale = (Rl)b.scale;
+        for (int e = tid; e < total; e += nt) {
+            const int mt = e % b.Mt;
+            int sf = e / b.Mt;
+            int64_t g = base + (int64_t)mt * b.stride[d - 1];
+            for (int l = d - 1; l >= 0; --l) {
+                const int sl = sf % b.p[l];
+                sf /= b.p[l];
+                g += (int64_t)sl * b.L[l] * b.stride[l];
+            }
+            C v = sm[e];
+            if (b.scale != 1.0) v = cscale(v, scale);
+            data[g] = v;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename C, int DIR>
+cudaError_t launch_b_t(const PhaseBFused &b, cudaStream_t st) {
+    size_t smem = (size_t)b.P * b.Mt * sizeof(C);
+    int64_t grid = b.tiles < (int64_t)1 << 30 ? b.tiles : (int64_t)1 << 30;
+    phase_b_fused_kernel<C, DIR><<<(unsigned)grid, b.threads, smem, st>>>(b);
+    return cudaGetLastError();
+}
+
+template <typename C, int DIR>
+cudaError_t prepare_b_t() {
+    return cudaFuncSetAttribute(phase_b_fused_kernel<C, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kMaxDynSmem);
+}
+
+}  // namespace
+
+cudaError_t prepare_phase_b_fused(int is_double, int dir) {
+    if (is_double) return dir < 0 ? prepare_b_t<double2, -1>() : prepare_b_t<double2, 1>();
+    return dir < 0 ? prepare_b_t<float2, -1>() : prepare_b_t<float2, 1>();
+}
+
+size_t phase_b_fused_smem_bytes(const PhaseBFused &b, int is_double) {
+    return (size_t)b.P * b.Mt * (is_double ? sizeof(double2) : sizeof(float2));
+}
+
+cudaError_t launch_phase_b_fused(const PhaseBFused &b, int is_double, int dir, cudaStream_t st) {
+    if (is_double) return dir < 0 ? launch_b_t<double2, -1>(b, st) : launch_b_t<double2, 1>(b, st);
+    return dir < 0 ? launch_b_t<float2, -1>(b, st) : launch_b_t<float2, 1>(b, st);
+}
+
+}  // namespace fftu

@@ -1,0 +1,70 @@
+"""The C-ABI library loads and exports every symbol include/fftu.h declares,
+and host-side validation rejects bad plans before touching a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fftu.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2203_11795_gb300 import _build
+    _build.build()
+    return ctypes.CDLL(_build.LIB)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fftu_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("fftu_plan", "fftu_exec", "fftu_destroy", "fftu_exec_phase", "fftu_status_string"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2203_11795_gb300 import _build
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (fftu_\w+)", out))
+    for name in declared_functions():
+        assert name in exported, name
+        assert hasattr(lib, name)
+    import paper_2203_11795_gb300 as f
+    assert set(f.EXPORTS) == set(declared_functions())
+
+
+def test_status_strings_and_version():
+    import paper_2203_11795_gb300 as f
+    for code in range(8):
+        assert f.fftu_status_string(code).startswith(f.STATUS_NAMES[code])
+    assert "sm_103a" in f.fftu_version()
+
+
+@pytest.mark.parametrize("n,p,code", [
+    ([64, 64, 64], [16, 2, 2], 2),   # 16^2 does not divide 64
+    ([48, 64], [4, 2], 3),           # 48 is valid for the method but not a power of two
+    ([64, 0], [1, 1], 1),            # n_l < 1
+    ([64, 64], [0, 1], 1),           # p_l < 1
+])
+def test_plan_validation(n, p, code):
+    import paper_2203_11795_gb300 as f
+    with pytest.raises(f.FFTUError) as ei:
+        f.fftu_plan(len(n), n, p, f.FFTU_C64, f.FFTU_FORWARD)
+    assert ei.value.status == code
+    assert f.fftu_last_error()
+
+
+def test_bad_dtype_dir_and_d():
+    import paper_2203_11795_gb300 as f
+    for args in ((0, [8], [1], 1, -1), (9, [2] * 9, [1] * 9, 1, -1), (1, [8], [1], 3, -1), (1, [8], [1], 1, 0)):
+        with pytest.raises(f.FFTUError) as ei:
+            f.fftu_plan(*args)
+        assert ei.value.status == 1  # FFTU_ERR_ARG

@@ -1,0 +1,177 @@
+"""GPU parity: the CUDA path against the FP64 oracle, element by element.
+
+Every case runs through the C ABI (fftu_plan / fftu_exec / fftu_exec_phase via
+the ctypes binding) on seeded inputs from fftu_inputs, and compares with the
+oracle on the exact same values (complex64 inputs are promoted exactly).
+Tolerance (relative L2 over the whole array): 1e-12 for complex128 and
+1e-5 * log2(N) for complex64.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from fftu_inputs import complex_uniform
+from oracle import cyclic_model as cm
+
+pytestmark = pytest.mark.gpu
+
+
+def tolerance(dtype, N):
+    return 1e-12 if np.dtype(dtype) == np.complex128 else 1e-5 * max(1.0, math.log2(N))
+
+
+@pytest.fixture(scope="module")
+def fftu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_11795_gb300 import _build
+    _build.build()
+    import paper_2203_11795_gb300 as f
+    return f
+
+
+def run_gpu(f, x, p, inverse=False, schedule=0, inplace=False, phase=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    with f.Plan(x.shape, p, dtype=t.dtype, inverse=inverse, schedule=schedule) as plan:
+        out = t if inplace else torch.empty_like(t)
+        if phase is None:
+            plan.exec(t, out)
+        elif phase == f.FFTU_PHASE_B:
+            out.copy_(t)
+            plan.exec_phase(phase, None, out)
+        else:
+            plan.exec_phase(phase, t, out)
+        torch.cuda.synchronize()
+        plan.check_device_status()
+        info = plan.info
+    return out.cpu().numpy(), info
+
+
+SMALL = [
+    # (shape, p, dtype)
+    ((64, 64, 64), (2, 2, 2), np.complex128),      # the 64^3 complex128 workload, p = 2x2x2
+    ((8, 8, 8), (2, 2, 2), np.complex64),
+    ((16, 16, 16), (4, 2, 1), np.complex64),
+    ((32, 64, 16), (4, 8, 2), np.complex64),
+    ((64, 64, 64), (4, 4, 4), np.complex64),
+    ((64, 64, 64), (8, 8, 8), np.complex64),
+    ((128, 32, 256), (8, 4, 16), np.complex64),
+    ((128,), (8,), np.complex64),                   # d = 1: Algorithm 2.2
+    ((4096,), (64,), np.complex64),                 # p_l > 16: per-axis phase B
+    ((256, 256), (16, 16), np.complex64),           # n_l = p_l^2
+    ((2, 1024, 8), (1, 16, 2), np.complex64),
+    ((16, 8, 4, 4, 2), (2, 2, 2, 2, 1), np.complex64),
+    ((8, 8, 8, 8), (2, 2, 2, 2), np.complex128),
+    ((16, 16, 16, 16), (4, 4, 4, 4), np.complex128),
+    ((1, 1, 64), (1, 1, 8), np.complex64),
+    ((2,), (1,), np.complex64),
+    ((1,), (1,), np.complex128),
+    ((4, 8, 16), (1, 1, 1), np.complex64),          # p = 1: phase B only scales
+]
+
+
+def _id(case):
+    shape, p, dt = case
+    return "x".join(map(str, shape)) + "_p" + "x".join(map(str, p)) + ("_c128" if dt == np.complex128 else "_c64")
+
+
+@pytest.mark.parametrize("case", SMALL, ids=_id)
+@pytest.mark.parametrize("inverse", [False, True])
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_matches_oracle(fftu, case, inverse, schedule):
+    shape, p, dt = case
+    x = complex_uniform(1000 + len(shape), shape, dtype=dt)
+    y, info = run_gpu(fftu, x, p, inverse=inverse, schedule=schedule)
+    ref = oracle.fftn(x.astype(np.complex128), inverse=inverse)
+    N = int(np.prod(shape))
+    err = oracle.rel_l2(y, ref)
+    assert err <= tolerance(dt, N), (err, info)
+
+
+@pytest.mark.parametrize("case", [((64, 64, 64), (4, 4, 4), np.complex64),
+                                  ((32, 16, 8), (2, 2, 2), np.complex128)], ids=_id)
+def test_in_place(fftu, case):
+    shape, p, dt = case
+    x = complex_uniform(77, shape, dtype=dt)
+    y, _ = run_gpu(fftu, x, p, inplace=True)
+    assert oracle.rel_l2(y, oracle.fftn(x.astype(np.complex128))) <= tolerance(dt, x.size)
+
+
+@pytest.mark.parametrize("case", [((16, 8, 32), (4, 2, 4), np.complex128),
+                                  ((64, 64, 64), (8, 8, 8), np.complex128),
+                                  ((64, 16), (8, 2), np.complex64)], ids=_id)
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_phases_match_model(fftu, case, schedule):
+    """Phase A alone = Supersteps 0+1 of the CPU model; phase B alone = Superstep 2."""
+    shape, p, dt = case
+    x = complex_uniform(88, shape, dtype=dt)
+    for inverse in (False, True):
+        wa, _ = run_gpu(fftu, x, p, inverse=inverse, schedule=schedule, phase=fftu.FFTU_PHASE_A)
+        w_ref = cm.phase_a(x.astype(np.complex128), p, inverse=inverse)
+        assert oracle.rel_l2(wa, w_ref) <= tolerance(dt, x.size)
+        w_in = w_ref.astype(dt)
+        vb, _ = run_gpu(fftu, w_in, p, inverse=inverse, schedule=schedule, phase=fftu.FFTU_PHASE_B)
+        v_ref = cm.phase_b(w_in.astype(np.complex128), p, inverse=inverse)
+        assert oracle.rel_l2(vb, v_ref) <= tolerance(dt, x.size)
+
+
+def test_round_trip_and_linearity(fftu):
+    import torch
+    shape, p = (128, 64, 32), (4, 4, 4)
+    x = torch.from_numpy(complex_uniform(5, shape, dtype=np.complex64)).cuda()
+    z = torch.from_numpy(complex_uniform(6, shape, dtype=np.complex64)).cuda()
+    with fftu.Plan(shape, p) as fwd, fftu.Plan(shape, p, inverse=True) as inv:
+        X, Z = fwd.exec(x), fwd.exec(z)
+        back = inv.exec(X)
+        lin = fwd.exec(2 * x - 3j * z)
+        torch.cuda.synchronize()
+    tol = tolerance(np.complex64, x.numel())
+    assert oracle.rel_l2(back.cpu().numpy(), x.cpu().numpy()) <= tol
+    assert oracle.rel_l2(lin.cpu().numpy(), (2 * X - 3j * Z).cpu().numpy()) <= tol
+
+
+def test_plan_info(fftu):
+    with fftu.Plan((64, 64, 64), (4, 4, 4)) as plan:
+        info = plan.info
+    assert info["N"] == 64 ** 3 and info["alg_bytes"] == 4 * 64 ** 3 * 8
+    assert info["p"] == [4, 4, 4] and info["launches_phase_a"] >= 1 and info["launches_phase_b"] >= 1
+    assert info["table_bytes"] == 3 * 64 * 8
+
+
+def test_exec_rejects_bad_pointers(fftu):
+    import torch
+    with fftu.Plan((16, 16), (2, 2)) as plan:
+        t = torch.zeros((16, 16), dtype=torch.complex64, device="cuda")
+        with pytest.raises(fftu.FFTUError) as ei:
+            fftu.fftu_exec(plan.handle, t.data_ptr() + 8, t.data_ptr(), 0)
+        assert ei.value.status == 1
+        with pytest.raises(fftu.FFTUError):
+            fftu.fftu_exec_phase(plan.handle, fftu.FFTU_PHASE_B, t.data_ptr() + 16, t.data_ptr(), 0)
+
+
+# ---- full-size workloads ------------------------------------------------------------------
+
+FULL = [((512, 512, 512), (8, 8, 8)), ((512, 512, 512), (4, 4, 4))]
+
+
+@pytest.mark.parametrize("shape,p", FULL, ids=["512c64_p8", "512c64_p4"])
+def test_full_size_512_forward_inverse(fftu, shape, p):
+    """512^3 complex64 forward against the full FP64 oracle, inverse by round trip."""
+    import torch
+    x = complex_uniform(2024, shape, dtype=np.complex64)
+    xt = torch.from_numpy(x).cuda()
+    with fftu.Plan(shape, p) as fwd, fftu.Plan(shape, p, inverse=True) as inv:
+        y = fwd.exec(xt)
+        back = inv.exec(y)
+        torch.cuda.synchronize()
+        fwd.check_device_status()
+        inv.check_device_status()
+    N = x.size
+    ref = oracle.fftn(x.astype(np.complex128))
+    assert oracle.rel_l2(y.cpu().numpy(), ref) <= tolerance(np.complex64, N)
+    del ref
+    assert oracle.rel_l2(back.cpu().numpy(), x) <= tolerance(np.complex64, N)
