@@ -6,8 +6,9 @@ below carry the C ABI's names (``include/fftu.h``) and take raw device
 pointers; ``Plan`` is a small convenience wrapper over torch tensors.  PyTorch
 supplies device memory and streams only.
 
-There is no CPU fallback: importing this package raises if the library has not
-been built, and every call raises ``FFTUError`` on a non-OK status.
+There is no CPU fallback: the first call into the library raises ImportError
+if ``libfftu.so`` has not been built, and every call raises ``FFTUError`` on a
+non-OK status.
 """
 from __future__ import annotations
 
@@ -75,7 +76,20 @@ def _load_library() -> ctypes.CDLL:
     return lib
 
 
-_lib = _load_library()
+class _LazyLib:
+    """Loads libfftu.so on first attribute access (so the build module can be
+    imported before the library exists); raises ImportError if it is missing."""
+
+    def __init__(self):
+        self._cdll = None
+
+    def __getattr__(self, name):
+        if self._cdll is None:
+            self._cdll = _load_library()
+        return getattr(self._cdll, name)
+
+
+_lib = _LazyLib()
 
 
 def _check(rc: int, where: str) -> None:
