@@ -65,7 +65,7 @@ int radix_plan(int len, int *radix) {
     return n;
 }
 
-enum StepKind { STEP_AXIS = 1, STEP_PHASE_B_FUSED = 2 };
+enum StepKind { STEP_AXIS = 1, STEP_PHASE_B_FUSED = 2, STEP_PHASE_B3 = 3 };
 
 struct Step {
     int kind;
@@ -186,7 +186,17 @@ fftu_status build_schedule(Plan &pl, int sched) {
     }
     // Phase B: one fused pass when every p_l <= 16, else one pass per axis.
     Step s;
-    if (sched != FFTU_SCHED_GENERIC && make_phase_b_fused(pl, scale, s.pb)) {
+    const int is_double = pl.dtype == FFTU_C128;
+    const int mt3 = pl.d == 3 && pl.p[0] == pl.p[1] && pl.p[1] == pl.p[2] && pl.p[0] > 1
+                        ? phase_b3_tile_mt((int)pl.p[0], is_double)
+                        : 0;
+    if (sched != FFTU_SCHED_GENERIC && mt3 > 0 && (pl.n[2] / pl.p[2]) % mt3 == 0 &&
+        make_phase_b_fused(pl, scale, s.pb)) {
+        s.kind = STEP_PHASE_B3;
+        s.pb.Mt = mt3;
+        s.pb.tiles = (pl.n[0] / pl.p[0]) * (pl.n[1] / pl.p[1]) * ((pl.n[2] / pl.p[2]) / mt3);
+        pl.phase_b.push_back(s);
+    } else if (sched != FFTU_SCHED_GENERIC && make_phase_b_fused(pl, scale, s.pb)) {
         s.kind = STEP_PHASE_B_FUSED;
         pl.phase_b.push_back(s);
     } else {
@@ -230,6 +240,10 @@ fftu_status run_steps(Plan *pl, const std::vector<Step> &steps, const void *firs
             a.src = src;
             a.dst = dst;
             e = launch_axis_pass(a, is_double, pl->dir, st);
+        } else if (s.kind == STEP_PHASE_B3) {
+            PhaseBFused b = s.pb;
+            b.data = dst;
+            e = launch_phase_b3(b, is_double, pl->dir, st);
         } else {
             PhaseBFused b = s.pb;
             b.data = dst;
@@ -372,6 +386,7 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
     }
     e = prepare_axis_pass(dtype == FFTU_C128, dir);
     if (e == cudaSuccess) e = prepare_phase_b_fused(dtype == FFTU_C128, dir);
+    if (e == cudaSuccess) e = prepare_phase_b3(dtype == FFTU_C128, dir);
     if (e != cudaSuccess) {
         free_plan(pl);
         return cuda_fail(e, "kernel attributes");
