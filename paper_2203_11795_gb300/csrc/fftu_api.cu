@@ -65,13 +65,20 @@ int radix_plan(int len, int *radix) {
     return n;
 }
 
-enum StepKind { STEP_AXIS = 1, STEP_PHASE_B_FUSED = 2, STEP_PHASE_B3 = 3 };
+enum StepKind { STEP_AXIS = 1, STEP_PHASE_B_FUSED = 2, STEP_PHASE_B3 = 3, STEP_PHASE_A3 = 4 };
 
 struct Step {
     int kind;
     AxisPass axis;
     PhaseBFused pb;
+    Phase3Launch a3;
 };
+
+// Residue units up to this size run phase A as one persistent kernel whose
+// scratch ring (kRingSlots units) is meant to stay resident in L2.
+constexpr int64_t kRingUnitMaxBytes = 16ll << 20;
+constexpr int kRingSlots = 3;
+constexpr long long kSpinLimitNs = 2000000000ll;
 
 }  // namespace
 
@@ -89,6 +96,7 @@ struct Plan {
     size_t workspace_bytes = 0;
     int *dstatus = nullptr;
     std::vector<Step> phase_a, phase_b;
+    std::vector<Step> phase_a_inplace;  // used when in == out and phase_a cannot run in place
 
     const void *table(int l) const { return static_cast<const char *>(tables) + table_off[l] * esize; }
 };
@@ -173,16 +181,81 @@ bool make_phase_b_fused(const Plan &pl, double scale, PhaseBFused &b) {
     return true;
 }
 
-fftu_status build_schedule(Plan &pl, int sched) {
-    const double scale = pl.dir == FFTU_INVERSE ? 1.0 / (double)pl.N : 1.0;
-    // Phase A: contiguous axis first (reads the caller's array in long runs).
+fftu_status build_generic_phase_a(Plan &pl, std::vector<Step> &out) {
+    // Contiguous axis first (reads the caller's array in long runs).
     for (int l = pl.d - 1; l >= 0; --l) {
         if (pl.n[l] == 1) continue;
         Step s;
         s.kind = STEP_AXIS;
         fftu_status st = make_axis_pass(pl, l, 0, 1.0, s.axis);
         if (st != FFTU_OK) return st;
-        pl.phase_a.push_back(s);
+        out.push_back(s);
+    }
+    return FFTU_OK;
+}
+
+// Fused 3D phase A when an instantiation matches; allocates the workspace.
+fftu_status build_fused_phase_a(Plan &pl, bool *used) {
+    *used = false;
+    Phase3Info info;
+    const int which = phase_a3_select(pl.d, pl.n, pl.p, pl.dtype == FFTU_C128, &info);
+    if (which < 0) return FFTU_OK;
+    Step s;
+    std::memset(&s.a3, 0, sizeof(s.a3));
+    s.kind = STEP_PHASE_A3;
+    Phase3Launch &l = s.a3;
+    l.which = which;
+    l.dir = pl.dir;
+    l.p0 = (int)pl.p[0];
+    l.p1 = (int)pl.p[1];
+    l.n0 = (int)pl.n[0];
+    l.n1 = (int)pl.n[1];
+    l.tw[0] = pl.table(0);
+    l.tw[1] = pl.table(1);
+    l.tw[2] = pl.table(2);
+    l.status = pl.dstatus;
+    l.spin_limit_ns = kSpinLimitNs;
+    size_t smem = 0;
+    cudaError_t e = prepare_phase_a3(which, pl.dir, l.n0, l.n1, &l.grid, &smem);
+    if (e != cudaSuccess) return cuda_fail(e, "fused phase A attributes");
+    const int64_t unit_bytes = info.unit_elems * (int64_t)pl.esize;
+    const int64_t units = pl.p[0] * pl.p[1];
+    size_t ws;
+    if (unit_bytes <= kRingUnitMaxBytes && units > kRingSlots) {
+        l.mode = 1;
+        l.ring = kRingSlots;
+        ws = (size_t)kRingSlots * unit_bytes + 256 + sizeof(unsigned) * (size_t)(1 + 2 * units);
+    } else {
+        l.mode = 0;
+        l.ring = 0;
+        ws = (size_t)pl.N * pl.esize;
+    }
+    e = cudaMalloc(&pl.workspace, ws);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_err("cudaMalloc of %zu workspace bytes: %s", ws, cudaGetErrorString(e));
+        return FFTU_ERR_NOMEM;
+    }
+    pl.workspace_bytes = ws;
+    l.scratch = pl.workspace;
+    if (l.mode == 1)
+        l.counters = reinterpret_cast<unsigned *>(static_cast<char *>(pl.workspace) +
+                                                  ((size_t)kRingSlots * unit_bytes + 255) / 256 * 256);
+    pl.phase_a.push_back(s);
+    *used = true;
+    return FFTU_OK;
+}
+
+fftu_status build_schedule(Plan &pl, int sched) {
+    const double scale = pl.dir == FFTU_INVERSE ? 1.0 / (double)pl.N : 1.0;
+    bool fused_a = false;
+    if (sched != FFTU_SCHED_GENERIC) {
+        fftu_status st = build_fused_phase_a(pl, &fused_a);
+        if (st != FFTU_OK) return st;
+    }
+    {
+        fftu_status st = build_generic_phase_a(pl, fused_a ? pl.phase_a_inplace : pl.phase_a);
+        if (st != FFTU_OK) return st;
     }
     // Phase B: one fused pass when every p_l <= 16, else one pass per axis.
     Step s;
@@ -217,6 +290,13 @@ fftu_status build_schedule(Plan &pl, int sched) {
     return FFTU_OK;
 }
 
+// Kernel launches one list of steps makes (the two-kernel fused phase A counts 2).
+int kernel_count(const std::vector<Step> &steps) {
+    int k = 0;
+    for (const Step &s : steps) k += (s.kind == STEP_PHASE_A3 && s.a3.mode == 0) ? 2 : 1;
+    return k;
+}
+
 void free_plan(Plan *pl) {
     if (!pl) return;
     if (pl->tables) cudaFree(pl->tables);
@@ -240,6 +320,11 @@ fftu_status run_steps(Plan *pl, const std::vector<Step> &steps, const void *firs
             a.src = src;
             a.dst = dst;
             e = launch_axis_pass(a, is_double, pl->dir, st);
+        } else if (s.kind == STEP_PHASE_A3) {
+            Phase3Launch l = s.a3;
+            l.in = src;
+            l.out = dst;
+            e = launch_phase_a3(l, st);
         } else if (s.kind == STEP_PHASE_B3) {
             PhaseBFused b = s.pb;
             b.data = dst;
@@ -445,7 +530,11 @@ fftu_status fftu_exec_phase(fftu_handle h, fftu_phase phase, const void *in, voi
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (phase & FFTU_PHASE_A) {
-        fftu_status s = run_steps(pl, pl->phase_a, in, out, st);
+        // the persistent phase-A kernel reads `in` while writing `out`; in place it
+        // would overwrite inputs other units have not read yet
+        const bool ring_inplace = in == out && !pl->phase_a_inplace.empty() && pl->phase_a.size() == 1 &&
+                                  pl->phase_a[0].kind == STEP_PHASE_A3 && pl->phase_a[0].a3.mode == 1;
+        fftu_status s = run_steps(pl, ring_inplace ? pl->phase_a_inplace : pl->phase_a, in, out, st);
         if (s != FFTU_OK) return s;
     }
     if (phase & FFTU_PHASE_B) {
@@ -495,8 +584,8 @@ fftu_status fftu_plan_info(fftu_handle h, fftu_info *info) {
     info->dtype = pl->dtype;
     info->dir = pl->dir;
     info->schedule = pl->schedule;
-    info->launches_phase_a = (int)pl->phase_a.size();
-    info->launches_phase_b = (int)pl->phase_b.size();
+    info->launches_phase_a = kernel_count(pl->phase_a);
+    info->launches_phase_b = kernel_count(pl->phase_b);
     info->N = pl->N;
     info->alg_bytes = 4 * pl->N * (int64_t)pl->esize;
     info->table_bytes = (int64_t)pl->table_bytes;

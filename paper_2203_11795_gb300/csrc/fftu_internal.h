@@ -56,6 +56,26 @@ struct PhaseBFused {
     double scale;
 };
 
+// Fused 3D phase A (complex64): see phase_a3.cu.
+struct Phase3Info {
+    int64_t unit_elems;  // elements of one residue unit (s0, s1)
+    int s1_tasks, s2_tasks;
+};
+struct Phase3Launch {
+    int which, dir, mode;  // mode 0: two kernels through a full workspace; 1: persistent L2 ring
+    const void *in;
+    void *out;
+    void *scratch;
+    const void *tw[3];
+    int *status;
+    unsigned *counters;
+    int p0, p1, n0, n1, ring, grid;
+    long long spin_limit_ns;
+};
+int phase_a3_select(int d, const int64_t *n, const int64_t *p, int is_double, Phase3Info *info);
+cudaError_t prepare_phase_a3(int which, int dir, int n0, int n1, int *grid, size_t *smem);
+cudaError_t launch_phase_a3(const Phase3Launch &l, cudaStream_t st);
+
 struct Plan;
 
 // Kernel launchers (return cudaGetLastError() of the launch).

@@ -1,0 +1,488 @@
+// Phase A for 3D complex64 arrays: Superstep 0 (local sub-FFTs of shape n/p
+// and the twiddle) and the Superstep 1 redistribution of Algorithm 2.3
+// (Sec. 2.2), in two stages that each read and write coalesced tiles.
+//
+// Axes are 0 (slowest), 1, 2 (contiguous); L_l = n_l / p_l.  The sub-FFT
+// along axis 1 is split by the radix split of Sec. 2.1.1 (eq. radix) as
+// L_1 = A * B, m_1 = a + A b:
+//     Y[c + B e] = sum_a w_A^{a e} [ w_{L_1}^{a c} sum_b X[a + A b] w_B^{b c} ].
+//
+// Stage 1, task (s0, s1, m0, a): the B rows i0 = s0 + p0 m0,
+//   i1 = s1 + p1 (a + A b), b in [B], read from HBM.
+//   * each row: F_{L_2} on every residue class s2 (i2 = s2 + p2 j), as
+//     L_2 = R1 * R2 (first radix-R1 stage straight from HBM in registers,
+//     shared exchange, radix-R2 stage), twiddle w_{n_2}^{k2 s2} and the Put
+//     position i2' = k2 + L_2 s2 (Superstep 1 along axis 2);
+//   * across the B rows: F_B over b and w_{L_1}^{a c}.
+//   The result T[c][i2'] goes to a scratch block laid out
+//   [c][i2' / W][m0][a][i2' % W], so that each stage-2 tile is contiguous.
+// Stage 2, task (s0, s1, c, chunk): the L_0 x A x W tile of T.
+//   * F_A over a, k1 = c + B e, twiddle w_{n_1}^{k1 s1};
+//   * F_{L_0} over m0 (L_0 = Q1 * Q2, two radix stages with one shared
+//     exchange), twiddle w_{n_0}^{k0 s0};
+//   * store at the Put position (k0 + L_0 s0, k1 + L_1 s1, i2') in HBM.
+// The twiddles of the three axes multiply to prod_l w_{n_l}^{k_l s_l}
+// (Algorithm 2.3, Superstep 0), and the three Put maps compose to the
+// Superstep 1 map m + s (n/p).
+//
+// Scheduling: either two kernels through a workspace of N elements
+// (stage 1 over all tasks, then stage 2), or one persistent kernel that walks
+// the units (s0, s1) in order, interleaving stage 1 of unit u + 1 with stage
+// 2 of unit u through a small ring of scratch slots meant to stay in L2; a
+// unit's stage-2 tasks wait for its stage-1 completion counter, and a slot is
+// reused only after the stage-2 tasks that read it have finished.  Waits are
+// bounded: a wait that expires sets the plan's status word to FFTU_ERR_TIMEOUT
+// and the task is skipped (the output is then invalid and the host reports it).
+#include <cuda_runtime.h>
+
+#include "fft_device.cuh"
+#include "fftu_internal.h"
+
+namespace fftu {
+
+namespace {
+
+template <int N2_, int P2_, int R1_, int B_, int A_, int L0_, int Q1_, int W_>
+struct Cfg {
+    static constexpr int N2 = N2_, P2 = P2_, L2 = N2 / P2, R1 = R1_, R2 = L2 / R1;
+    static constexpr int B = B_, A = A_, L1 = A * B;
+    static constexpr int L0 = L0_, Q1 = Q1_, Q2 = L0 / Q1;
+    static constexpr int W = W_, NCH = N2 / W;
+    static constexpr int NT = 512;
+    static constexpr int TILE1 = B * N2;        // stage-1 elements
+    static constexpr int TILE2 = L0 * A * W;    // stage-2 elements
+    static constexpr int TILE = TILE1 > TILE2 ? TILE1 : TILE2;
+    static constexpr int UNIT = L0 * L1 * N2;   // elements of one residue unit (s0, s1)
+    static constexpr int S1_TASKS = L0 * A;     // stage-1 tasks per unit
+    static constexpr int S2_TASKS = B * NCH;    // stage-2 tasks per unit
+    // shared swizzle widths (8-byte words per 128-byte wavefront = 16)
+    static constexpr int SW1 = (16 / P2) < R2 ? (16 / P2) : R2;
+};
+
+// Run-time geometry shared by every task.
+struct Geo {
+    const float2 *in;
+    float2 *out;
+    float2 *scratch;       // workspace (two-kernel mode: N elements; ring mode: ring slots)
+    const float2 *tw0, *tw1, *tw2;  // w_{n_l}^e tables
+    int *status;
+    unsigned *counters;    // ring mode: [0] task counter, [1..U] stage-1 done, [U+1..2U] stage-2 done
+    int P0, P1;            // p_0, p_1
+    int n0, n1;            // n_0 = P0 L0, n1 = P1 L1
+    int units;             // P0 * P1
+    int ring;              // ring slots (ring mode)
+    long long spin_limit;  // bounded-wait budget in nanoseconds
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for counters[idx] >= target (one thread); false on timeout.
+__device__ bool wait_counter(const unsigned *ctr, unsigned target, long long limit_ns, int *status) {
+    const unsigned long long t0 = global_ns();
+    unsigned v;
+    for (;;) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= target) return true;
+        if ((long long)(global_ns() - t0) > limit_ns) {
+            atomicCAS(status, 0, (int)FFTU_ERR_TIMEOUT);
+            return false;
+        }
+        __nanosleep(64);
+    }
+}
+
+template <int DIR> __device__ __forceinline__ float2 tw_at(const float2 *t, int e) { return dirw<DIR>(t[e]); }
+
+// ---- stage 1 ----------------------------------------------------------------------------------
+// sm: TILE1 elements.  Shared layouts:
+//   X1[b][u][q'][s2] with q' = q ^ (u mod SW1)        (exchange inside each row FFT)
+//   X2[b][i2''] with i2'' = L2 s2 + (k2 ^ sigma(s2))    (Put order, swizzled)
+template <class K, int DIR>
+__device__ __forceinline__ int x2_index(int b, int k2, int s2) {
+    constexpr int sig = 16 / K::P2 > 1 ? 16 / K::P2 : 1;
+    const int sw = (s2 * sig) & (K::L2 - 1) & 15;
+    return b * K::N2 + K::L2 * s2 + (k2 ^ sw);
+}
+
+template <class K, int DIR>
+__device__ void stage1_task(const Geo &g, float2 *sm, const float2 *s_tw0, const float2 *s_tw1,
+                            const float2 *s_tw2, int s0, int s1, int m0, int a, float2 *dst_unit) {
+    const int tid = threadIdx.x;
+    const int i0 = s0 + g.P0 * m0;
+    const float2 *plane = g.in + (size_t)i0 * g.n1 * K::N2;
+    // S1a: items (b, s2, q), s2 fastest; inputs j = q + R2 r -> i2 = s2 + P2 q + (N2 / R1) r
+    constexpr int IA = K::B * K::P2 * K::R2;
+    static_assert(IA % K::NT == 0 || K::NT % IA == 0, "stage-1a items");
+    for (int it = tid; it < IA; it += K::NT) {
+        const int s2 = it % K::P2, q = (it / K::P2) % K::R2, b = it / (K::P2 * K::R2);
+        const int i1 = s1 + g.P1 * (a + K::A * b);
+        const float2 *row = plane + (size_t)i1 * K::N2;
+        float2 v[K::R1];
+#pragma unroll
+        for (int r = 0; r < K::R1; ++r) v[r] = __ldcs(row + s2 + K::P2 * q + (K::N2 / K::R1) * r);
+        dft_small<K::R1, DIR>(v);
+#pragma unroll
+        for (int u = 0; u < K::R1; ++u) {
+            float2 x = v[u];
+            if (u != 0 && q != 0) x = cmul(x, tw_at<DIR>(s_tw2, (q * u * K::P2) & (K::N2 - 1)));
+            const int qq = q ^ (u % K::SW1);
+            sm[((b * K::R1 + u) * K::R2 + qq) * K::P2 + s2] = x;
+        }
+    }
+    __syncthreads();
+    // S1b: items (b, s2, u), s2 fastest; F_{R2} over q -> v; k2 = u + R1 v
+    constexpr int IB = K::B * K::P2 * K::R1;
+    constexpr int NB = (IB + K::NT - 1) / K::NT;
+    float2 hold[NB][K::R2];
+#pragma unroll
+    for (int h = 0; h < NB; ++h) {
+        const int it = tid + h * K::NT;
+        if (it < IB) {
+            const int s2 = it % K::P2, u = (it / K::P2) % K::R1, b = it / (K::P2 * K::R1);
+#pragma unroll
+            for (int q = 0; q < K::R2; ++q)
+                hold[h][q] = sm[((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + s2];
+            dft_small<K::R2, DIR>(hold[h]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < NB; ++h) {
+        const int it = tid + h * K::NT;
+        if (it < IB) {
+            const int s2 = it % K::P2, u = (it / K::P2) % K::R1, b = it / (K::P2 * K::R1);
+#pragma unroll
+            for (int vv = 0; vv < K::R2; ++vv) {
+                const int k2 = u + K::R1 * vv;
+                float2 x = hold[h][vv];
+                if (k2 != 0 && s2 != 0) x = cmul(x, tw_at<DIR>(s_tw2, k2 * s2));
+                sm[x2_index<K, DIR>(b, k2, s2)] = x;
+            }
+        }
+    }
+    __syncthreads();
+    // S1c: items i2' (Put order); F_B over b -> c; twiddle w_{L1}^{a c}; store to scratch
+    for (int ip = tid; ip < K::N2; ip += K::NT) {
+        const int s2 = ip / K::L2, k2 = ip % K::L2;
+        float2 v[K::B];
+#pragma unroll
+        for (int b = 0; b < K::B; ++b) v[b] = sm[x2_index<K, DIR>(b, k2, s2)];
+        dft_small<K::B, DIR>(v);
+        const int chunk = ip / K::W, w = ip % K::W;
+        float2 *d = dst_unit + (((size_t)chunk * K::L0 + m0) * K::A + a) * K::W + w;
+#pragma unroll
+        for (int c = 0; c < K::B; ++c) {
+            float2 x = v[c];
+            if (a != 0 && c != 0) x = cmul(x, tw_at<DIR>(s_tw1, (a * c * g.P1) & (g.n1 - 1)));
+            d[(size_t)c * K::NCH * K::L0 * K::A * K::W] = x;
+        }
+    }
+}
+
+// ---- stage 2 ----------------------------------------------------------------------------------
+// sm: TILE2 elements.  Shared layouts: Y1[e][m0][w]; Y2[e][u'][q'][w].
+template <class K, int DIR, bool CG>
+__device__ void stage2_task(const Geo &g, float2 *sm, const float2 *s_tw0, const float2 *s_tw1,
+                            const float2 *s_tw2, int s0, int s1, int c, int chunk, const float2 *src_unit) {
+    const int tid = threadIdx.x;
+    const float2 *blk = src_unit + ((size_t)c * K::NCH + chunk) * K::L0 * K::A * K::W;
+    // S2a: items (m0, w), w fastest; F_A over a -> e; k1 = c + B e; twiddle w_{n1}^{k1 s1}
+    constexpr int IA = K::L0 * K::W;
+    for (int it = tid; it < IA; it += K::NT) {
+        const int w = it % K::W, m0 = it / K::W;
+        float2 v[K::A];
+#pragma unroll
+        for (int a = 0; a < K::A; ++a) {
+            const float2 *p = blk + ((size_t)m0 * K::A + a) * K::W + w;
+            v[a] = CG ? __ldcg(p) : __ldcs(p);
+        }
+        dft_small<K::A, DIR>(v);
+#pragma unroll
+        for (int e = 0; e < K::A; ++e) {
+            const int k1 = c + K::B * e;
+            float2 x = v[e];
+            if (k1 != 0 && s1 != 0) x = cmul(x, tw_at<DIR>(s_tw1, (k1 * s1) & (g.n1 - 1)));
+            sm[(e * K::L0 + m0) * K::W + w] = x;
+        }
+    }
+    __syncthreads();
+    // S2b: items (e, q', w), w fastest; m0 = q' + Q2 r; F_{Q1} over r -> u'; twiddle w_{L0}^{q' u'}
+    constexpr int IB = K::A * K::Q2 * K::W;
+    constexpr int NB = (IB + K::NT - 1) / K::NT;
+    float2 hold[NB][K::Q1];
+#pragma unroll
+    for (int h = 0; h < NB; ++h) {
+        const int it = tid + h * K::NT;
+        if (it < IB) {
+            const int w = it % K::W, q = (it / K::W) % K::Q2, e = it / (K::W * K::Q2);
+#pragma unroll
+            for (int r = 0; r < K::Q1; ++r) hold[h][r] = sm[(e * K::L0 + q + K::Q2 * r) * K::W + w];
+            dft_small<K::Q1, DIR>(hold[h]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < NB; ++h) {
+        const int it = tid + h * K::NT;
+        if (it < IB) {
+            const int w = it % K::W, q = (it / K::W) % K::Q2, e = it / (K::W * K::Q2);
+#pragma unroll
+            for (int u = 0; u < K::Q1; ++u) {
+                float2 x = hold[h][u];
+                if (u != 0 && q != 0) x = cmul(x, tw_at<DIR>(s_tw0, (q * u * g.P0) & (g.n0 - 1)));
+                sm[((e * K::Q1 + u) * K::Q2 + q) * K::W + w] = x;
+            }
+        }
+    }
+    __syncthreads();
+    // S2c: items (e, u', w), w fastest; F_{Q2} over q' -> v'; k0 = u' + Q1 v'; twiddle w_{n0}^{k0 s0}
+    constexpr int IC = K::A * K::Q1 * K::W;
+    for (int it = tid; it < IC; it += K::NT) {
+        const int w = it % K::W, u = (it / K::W) % K::Q1, e = it / (K::W * K::Q1);
+        float2 v[K::Q2];
+#pragma unroll
+        for (int q = 0; q < K::Q2; ++q) v[q] = sm[((e * K::Q1 + u) * K::Q2 + q) * K::W + w];
+        dft_small<K::Q2, DIR>(v);
+        const int k1 = c + K::B * e;
+        float2 *dst = g.out + ((size_t)(k1 + K::L1 * s1) * K::N2 + (size_t)chunk * K::W + w);
+#pragma unroll
+        for (int vv = 0; vv < K::Q2; ++vv) {
+            const int k0 = u + K::Q1 * vv;
+            float2 x = v[vv];
+            if (k0 != 0 && s0 != 0) x = cmul(x, tw_at<DIR>(s_tw0, (k0 * s0) & (g.n0 - 1)));
+            __stcs(dst + (size_t)(k0 + K::L0 * s0) * g.n1 * K::N2, x);
+        }
+    }
+}
+
+template <class K>
+__device__ void load_tables(const Geo &g, float2 *s_tw0, float2 *s_tw1, float2 *s_tw2) {
+    for (int e = threadIdx.x; e < g.n0; e += blockDim.x) s_tw0[e] = g.tw0[e];
+    for (int e = threadIdx.x; e < g.n1; e += blockDim.x) s_tw1[e] = g.tw1[e];
+    for (int e = threadIdx.x; e < K::N2; e += blockDim.x) s_tw2[e] = g.tw2[e];
+    __syncthreads();
+}
+
+// Shared memory: tables (n0 + n1 + N2 entries) then the tile.
+template <class K, int DIR>
+__global__ void __launch_bounds__(K::NT) stage1_kernel(const __grid_constant__ Geo g) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *s_tw0 = reinterpret_cast<float2 *>(smem_raw);
+    float2 *s_tw1 = s_tw0 + g.n0, *s_tw2 = s_tw1 + g.n1, *sm = s_tw2 + K::N2;
+    load_tables<K>(g, s_tw0, s_tw1, s_tw2);
+    const int total = g.units * K::S1_TASKS;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int unit = t / K::S1_TASKS, lt = t % K::S1_TASKS;
+        const int s0 = unit / g.P1, s1 = unit % g.P1;
+        const int m0 = lt / K::A, a = lt % K::A;
+        stage1_task<K, DIR>(g, sm, s_tw0, s_tw1, s_tw2, s0, s1, m0, a, g.scratch + (size_t)unit * K::UNIT);
+        __syncthreads();
+    }
+}
+
+template <class K, int DIR>
+__global__ void __launch_bounds__(K::NT) stage2_kernel(const __grid_constant__ Geo g) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *s_tw0 = reinterpret_cast<float2 *>(smem_raw);
+    float2 *s_tw1 = s_tw0 + g.n0, *s_tw2 = s_tw1 + g.n1, *sm = s_tw2 + K::N2;
+    load_tables<K>(g, s_tw0, s_tw1, s_tw2);
+    const int total = g.units * K::S2_TASKS;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int unit = t / K::S2_TASKS, lt = t % K::S2_TASKS;
+        const int s0 = unit / g.P1, s1 = unit % g.P1;
+        const int c = lt / K::NCH, chunk = lt % K::NCH;
+        stage2_task<K, DIR, false>(g, sm, s_tw0, s_tw1, s_tw2, s0, s1, c, chunk,
+                                   g.scratch + (size_t)unit * K::UNIT);
+        __syncthreads();
+    }
+}
+
+// Persistent ring kernel.  Task order: S1(0), S1(1), S2(0), S1(2), S2(1), ..., S2(U-1).
+template <class K, int DIR>
+__global__ void __launch_bounds__(K::NT) ring_kernel(const __grid_constant__ Geo g) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *s_tw0 = reinterpret_cast<float2 *>(smem_raw);
+    float2 *s_tw1 = s_tw0 + g.n0, *s_tw2 = s_tw1 + g.n1, *sm = s_tw2 + K::N2;
+    __shared__ int s_task;
+    __shared__ int s_ok;
+    load_tables<K>(g, s_tw0, s_tw1, s_tw2);
+    const int U = g.units;
+    const int total = U * (K::S1_TASKS + K::S2_TASKS);
+    unsigned *task_ctr = g.counters;
+    unsigned *s1_done = g.counters + 1;
+    unsigned *s2_done = g.counters + 1 + U;
+    for (;;) {
+        if (threadIdx.x == 0) s_task = (int)atomicAdd(task_ctr, 1u);
+        __syncthreads();
+        const int t = s_task;
+        if (t >= total) break;
+        // decode: group 0 = S1(0); group j >= 1 = S1(j) (if j < U) followed by S2(j - 1)
+        int unit, lt, is_s1;
+        if (t < K::S1_TASKS) {
+            unit = 0;
+            lt = t;
+            is_s1 = 1;
+        } else {
+            const int r = t - K::S1_TASKS;
+            const int grp = K::S1_TASKS + K::S2_TASKS;
+            const int j = r / grp + 1, o = r % grp;
+            if (j < U && o < K::S1_TASKS) {
+                unit = j;
+                lt = o;
+                is_s1 = 1;
+            } else {
+                unit = j - 1;
+                lt = j < U ? o - K::S1_TASKS : o;
+                is_s1 = 0;
+            }
+        }
+        const int s0 = unit / g.P1, s1 = unit % g.P1;
+        float2 *slot = g.scratch + (size_t)(unit % g.ring) * K::UNIT;
+        if (threadIdx.x == 0) {
+            bool ok = true;
+            if (is_s1) {
+                if (unit >= g.ring) ok = wait_counter(s2_done + (unit - g.ring), K::S2_TASKS, g.spin_limit, g.status);
+            } else {
+                ok = wait_counter(s1_done + unit, K::S1_TASKS, g.spin_limit, g.status);
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (s_ok) {
+            if (is_s1) {
+                stage1_task<K, DIR>(g, sm, s_tw0, s_tw1, s_tw2, s0, s1, lt / K::A, lt % K::A, slot);
+            } else {
+                stage2_task<K, DIR, true>(g, sm, s_tw0, s_tw1, s_tw2, s0, s1, lt / K::NCH, lt % K::NCH, slot);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(is_s1 ? s1_done + unit : s2_done + unit, 1u);
+        }
+    }
+}
+
+// ---- host side --------------------------------------------------------------------------------
+
+template <class K>
+size_t smem_bytes(int n0, int n1) {
+    return (size_t)(n0 + n1 + K::N2 + K::TILE) * sizeof(float2);
+}
+
+template <class K, int DIR>
+cudaError_t launch_k(const Phase3Launch &l, cudaStream_t st) {
+    Geo g;
+    g.in = static_cast<const float2 *>(l.in);
+    g.out = static_cast<float2 *>(l.out);
+    g.scratch = static_cast<float2 *>(l.scratch);
+    g.tw0 = static_cast<const float2 *>(l.tw[0]);
+    g.tw1 = static_cast<const float2 *>(l.tw[1]);
+    g.tw2 = static_cast<const float2 *>(l.tw[2]);
+    g.status = l.status;
+    g.counters = l.counters;
+    g.P0 = l.p0;
+    g.P1 = l.p1;
+    g.n0 = l.n0;
+    g.n1 = l.n1;
+    g.units = l.p0 * l.p1;
+    g.ring = l.ring;
+    g.spin_limit = l.spin_limit_ns;
+    const size_t smem = smem_bytes<K>(l.n0, l.n1);
+    if (l.mode == 0) {
+        int grid1 = g.units * K::S1_TASKS, grid2 = g.units * K::S2_TASKS;
+        if (grid1 > l.grid) grid1 = l.grid;
+        if (grid2 > l.grid) grid2 = l.grid;
+        stage1_kernel<K, DIR><<<grid1, K::NT, smem, st>>>(g);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        stage2_kernel<K, DIR><<<grid2, K::NT, smem, st>>>(g);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaMemsetAsync(l.counters, 0, sizeof(unsigned) * (1 + 2 * (size_t)g.units), st);
+    if (e != cudaSuccess) return e;
+    ring_kernel<K, DIR><<<l.grid, K::NT, smem, st>>>(g);
+    return cudaGetLastError();
+}
+
+template <class K, int DIR>
+cudaError_t prepare_k(int n0, int n1, int *grid_out) {
+    const size_t smem = smem_bytes<K>(n0, n1);
+    cudaError_t e = cudaFuncSetAttribute(stage1_kernel<K, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stage2_kernel<K, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ring_kernel<K, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ring_kernel<K, DIR>, K::NT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    *grid_out = sms * per_sm;
+    return cudaSuccess;
+}
+
+// Instantiated configurations (complex64):
+//   512^3, p = 8^3: L = 64, rows 64 = 8 x 8, axis 1 = 8 x 8, axis 0 = 8 x 8, W = 16
+//   512^3, p = 4^3: L = 128, rows 128 = 16 x 8, axis 1 = 8 x 16, axis 0 = 16 x 8, W = 8
+using K512p8 = Cfg<512, 8, 8, 8, 8, 64, 8, 16>;
+using K512p4 = Cfg<512, 4, 16, 16, 8, 128, 16, 8>;
+
+template <int DIR, bool PREP>
+cudaError_t dispatch(int which, const Phase3Launch *l, cudaStream_t st, int n0, int n1, int *grid, size_t *smem) {
+    switch (which) {
+        case 0:
+            if (smem) *smem = smem_bytes<K512p8>(n0, n1);
+            return PREP ? prepare_k<K512p8, DIR>(n0, n1, grid) : launch_k<K512p8, DIR>(*l, st);
+        case 1:
+            if (smem) *smem = smem_bytes<K512p4>(n0, n1);
+            return PREP ? prepare_k<K512p4, DIR>(n0, n1, grid) : launch_k<K512p4, DIR>(*l, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class K>
+bool matches(const int64_t *n, const int64_t *p) {
+    return n[2] == K::N2 && p[2] == K::P2 && n[1] / p[1] == K::L1 && n[0] / p[0] == K::L0;
+}
+
+template <class K>
+void fill(Phase3Info &info) {
+    info.unit_elems = K::UNIT;
+    info.s1_tasks = K::S1_TASKS;
+    info.s2_tasks = K::S2_TASKS;
+}
+
+}  // namespace
+
+int phase_a3_select(int d, const int64_t *n, const int64_t *p, int is_double, Phase3Info *info) {
+    if (d != 3 || is_double) return -1;
+    if (n[0] > (1 << 20) || n[1] > (1 << 20)) return -1;
+    if (matches<K512p8>(n, p)) {
+        fill<K512p8>(*info);
+        return 0;
+    }
+    if (matches<K512p4>(n, p)) {
+        fill<K512p4>(*info);
+        return 1;
+    }
+    return -1;
+}
+
+cudaError_t prepare_phase_a3(int which, int dir, int n0, int n1, int *grid, size_t *smem) {
+    return dir < 0 ? dispatch<-1, true>(which, nullptr, 0, n0, n1, grid, smem)
+                   : dispatch<1, true>(which, nullptr, 0, n0, n1, grid, smem);
+}
+
+cudaError_t launch_phase_a3(const Phase3Launch &l, cudaStream_t st) {
+    return l.dir < 0 ? dispatch<-1, false>(l.which, &l, st, l.n0, l.n1, nullptr, nullptr)
+                     : dispatch<1, false>(l.which, &l, st, l.n0, l.n1, nullptr, nullptr);
+}
+
+}  // namespace fftu
