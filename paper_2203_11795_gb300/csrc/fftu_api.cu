@@ -216,7 +216,11 @@ fftu_status build_fused_phase_a(Plan &pl, bool *used) {
     l.status = pl.dstatus;
     l.spin_limit_ns = kSpinLimitNs;
     size_t smem = 0;
-    cudaError_t e = prepare_phase_a3(which, pl.dir, l.n0, l.n1, &l.grid, &smem);
+    int grids[3] = {0, 0, 0};
+    cudaError_t e = prepare_phase_a3(which, pl.dir, l.n0, l.n1, grids, &smem);
+    l.grid1 = grids[0];
+    l.grid2 = grids[1];
+    l.grid = grids[2];
     if (e != cudaSuccess) return cuda_fail(e, "fused phase A attributes");
     const int64_t unit_bytes = info.unit_elems * (int64_t)pl.esize;
     const int64_t units = pl.p[0] * pl.p[1];

@@ -69,11 +69,13 @@ struct Phase3Launch {
     const void *tw[3];
     int *status;
     unsigned *counters;
-    int p0, p1, n0, n1, ring, grid;
+    int p0, p1, n0, n1, ring;
+    int grid, grid1, grid2;  // persistent ring kernel; stage-1 and stage-2 kernels
     long long spin_limit_ns;
 };
 int phase_a3_select(int d, const int64_t *n, const int64_t *p, int is_double, Phase3Info *info);
-cudaError_t prepare_phase_a3(int which, int dir, int n0, int n1, int *grid, size_t *smem);
+// grids[0..2]: stage-1, stage-2 and ring kernel grid sizes (SMs x resident CTAs).
+cudaError_t prepare_phase_a3(int which, int dir, int n0, int n1, int *grids, size_t *smem);
 cudaError_t launch_phase_a3(const Phase3Launch &l, cudaStream_t st);
 
 struct Plan;

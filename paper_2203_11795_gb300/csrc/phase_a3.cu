@@ -269,7 +269,7 @@ __device__ void load_tables(const Geo &g, float2 *s_tw0, float2 *s_tw1, float2 *
 
 // Shared memory: tables (n0 + n1 + N2 entries) then the tile.
 template <class K, int DIR>
-__global__ void __launch_bounds__(K::NT) stage1_kernel(const __grid_constant__ Geo g) {
+__global__ void __launch_bounds__(K::NT, 2) stage1_kernel(const __grid_constant__ Geo g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *s_tw0 = reinterpret_cast<float2 *>(smem_raw);
     float2 *s_tw1 = s_tw0 + g.n0, *s_tw2 = s_tw1 + g.n1, *sm = s_tw2 + K::N2;
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(K::NT) stage1_kernel(const __grid_constant__ G
 }
 
 template <class K, int DIR>
-__global__ void __launch_bounds__(K::NT) stage2_kernel(const __grid_constant__ Geo g) {
+__global__ void __launch_bounds__(K::NT, 2) stage2_kernel(const __grid_constant__ Geo g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *s_tw0 = reinterpret_cast<float2 *>(smem_raw);
     float2 *s_tw1 = s_tw0 + g.n0, *s_tw2 = s_tw1 + g.n1, *sm = s_tw2 + K::N2;
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(K::NT) stage2_kernel(const __grid_constant__ G
 
 // Persistent ring kernel.  Task order: S1(0), S1(1), S2(0), S1(2), S2(1), ..., S2(U-1).
 template <class K, int DIR>
-__global__ void __launch_bounds__(K::NT) ring_kernel(const __grid_constant__ Geo g) {
+__global__ void __launch_bounds__(K::NT, 2) ring_kernel(const __grid_constant__ Geo g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *s_tw0 = reinterpret_cast<float2 *>(smem_raw);
     float2 *s_tw1 = s_tw0 + g.n0, *s_tw2 = s_tw1 + g.n1, *sm = s_tw2 + K::N2;
@@ -395,8 +395,8 @@ cudaError_t launch_k(const Phase3Launch &l, cudaStream_t st) {
     const size_t smem = smem_bytes<K>(l.n0, l.n1);
     if (l.mode == 0) {
         int grid1 = g.units * K::S1_TASKS, grid2 = g.units * K::S2_TASKS;
-        if (grid1 > l.grid) grid1 = l.grid;
-        if (grid2 > l.grid) grid2 = l.grid;
+        if (grid1 > l.grid1) grid1 = l.grid1;
+        if (grid2 > l.grid2) grid2 = l.grid2;
         stage1_kernel<K, DIR><<<grid1, K::NT, smem, st>>>(g);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -409,23 +409,30 @@ cudaError_t launch_k(const Phase3Launch &l, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <class K, int DIR>
-cudaError_t prepare_k(int n0, int n1, int *grid_out) {
-    const size_t smem = smem_bytes<K>(n0, n1);
-    cudaError_t e = cudaFuncSetAttribute(stage1_kernel<K, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(stage2_kernel<K, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ring_kernel<K, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// Raise the dynamic shared-memory limit, prefer the largest shared carveout,
+// and return SMs x resident CTAs per SM for one kernel.
+template <typename F>
+cudaError_t setup_kernel(F *fn, int nt, size_t smem, int *grid_out) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ring_kernel<K, DIR>, K::NT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     *grid_out = sms * per_sm;
     return cudaSuccess;
+}
+
+template <class K, int DIR>
+cudaError_t prepare_k(int n0, int n1, int *grids) {
+    const size_t smem = smem_bytes<K>(n0, n1);
+    cudaError_t e = setup_kernel(stage1_kernel<K, DIR>, K::NT, smem, &grids[0]);
+    if (e == cudaSuccess) e = setup_kernel(stage2_kernel<K, DIR>, K::NT, smem, &grids[1]);
+    if (e == cudaSuccess) e = setup_kernel(ring_kernel<K, DIR>, K::NT, smem, &grids[2]);
+    return e;
 }
 
 // Instantiated configurations (complex64):
