@@ -153,6 +153,29 @@ fftu_status fftu_plan_info(fftu_handle plan, fftu_info *info);
  * FFTU_ERR_TIMEOUT or FFTU_ERR_INTERNAL. */
 fftu_status fftu_check_device_status(fftu_handle plan);
 
+/*
+ * fftu_exec_noalloc -- the whole transform with no device allocation at all.
+ * The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc where they run the FFT (code under CUDA graph capture, plugins
+ * whose host owns all device memory, real-time loops that must not enter the
+ * allocator).  No plan is needed; the arguments mean what they mean for
+ * fftu_plan and fftu_exec, with these limits:
+ *   - d = 3, FFTU_C64, p_0 = p_1 = p_2, and a shape with a fused kernel whose
+ *     residue unit (n_0 n_1 n_2 / (p_0 p_1) elements) fits a 16 MiB slot
+ *     (e.g. 512^3 with p = 8^3); otherwise FFTU_ERR_UNSUPPORTED;
+ *   - in != out (FFTU_ERR_ARG otherwise); both 16-byte aligned device pointers.
+ * Scratch, counters and twiddle tables live in static device arrays (about
+ * 32 MiB, held by every GPU that loads this part of the library until the
+ * process exits).  The first call on a device (with that device current) looks
+ * up their addresses; make it before any stream capture.  All calls share the
+ * arrays: calls that overlap on the GPU race and give wrong results, so order
+ * them on one stream.  The counters are cleared and the tables rewritten on the
+ * stream by each call as needed.  Calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ */
+fftu_status fftu_exec_noalloc(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,
+                              const void *in, void *out, void *stream);
+
 /* Static string for a status code. */
 const char *fftu_status_string(fftu_status s);
 

@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "FFTU_OK", 1: "FFTU_ERR_ARG", 2: "FFTU_ERR_DIVISIBILITY", 3: 
 
 # Every entry point the header declares (checked by the test suite).
 EXPORTS = ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_destroy", "fftu_plan_info",
-           "fftu_check_device_status", "fftu_status_string", "fftu_last_error", "fftu_version")
+           "fftu_check_device_status", "fftu_exec_noalloc", "fftu_status_string", "fftu_last_error",
+           "fftu_version")
 
 
 class FFTUError(RuntimeError):
@@ -66,12 +67,13 @@ def _load_library() -> ctypes.CDLL:
     lib.fftu_destroy.argtypes = [h]
     lib.fftu_plan_info.argtypes = [h, ctypes.POINTER(fftu_info)]
     lib.fftu_check_device_status.argtypes = [h]
+    lib.fftu_exec_noalloc.argtypes = [ctypes.c_int, i64p, i64p, ctypes.c_int, ctypes.c_int, vp, vp, vp]
     lib.fftu_status_string.argtypes = [ctypes.c_int]
     lib.fftu_status_string.restype = ctypes.c_char_p
     lib.fftu_last_error.restype = ctypes.c_char_p
     lib.fftu_version.restype = ctypes.c_char_p
     for name in ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_destroy",
-                 "fftu_plan_info", "fftu_check_device_status"):
+                 "fftu_plan_info", "fftu_check_device_status", "fftu_exec_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -143,6 +145,13 @@ def fftu_plan_info(plan: int) -> dict:
 
 def fftu_check_device_status(plan: int) -> None:
     _check(_lib.fftu_check_device_status(plan), "fftu_check_device_status")
+
+
+def fftu_exec_noalloc(d: int, n, p, dtype: int, direction: int, in_ptr: int, out_ptr: int,
+                      stream: int = 0) -> None:
+    """Whole transform with no device allocation (static device scratch); see include/fftu.h."""
+    _check(_lib.fftu_exec_noalloc(int(d), _i64(n), _i64(p), int(dtype), int(direction), in_ptr, out_ptr,
+                                  stream or None), "fftu_exec_noalloc")
 
 
 def fftu_status_string(status: int) -> str:

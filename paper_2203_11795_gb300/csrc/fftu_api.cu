@@ -32,6 +32,12 @@ void set_err(const char *fmt, ...) {
     va_end(ap);
 }
 
+}  // namespace
+
+void record_error(const char *msg) { set_err("%s", msg); }
+
+namespace {
+
 fftu_status cuda_fail(cudaError_t e, const char *what) {
     set_err("%s: %s", what, cudaGetErrorString(e));
     return FFTU_ERR_CUDA;

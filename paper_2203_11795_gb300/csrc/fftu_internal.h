@@ -80,6 +80,9 @@ cudaError_t launch_phase_a3(const Phase3Launch &l, cudaStream_t st);
 
 struct Plan;
 
+// Set the calling thread's detail string returned by fftu_last_error().
+void record_error(const char *msg);
+
 // Kernel launchers (return cudaGetLastError() of the launch).
 // Set per-device kernel attributes (dynamic shared memory); called at plan time.
 cudaError_t prepare_axis_pass(int is_double, int dir);
