@@ -81,42 +81,37 @@ template <int DIR, typename C> __device__ __forceinline__ void dft8(C *v) {
 template <int DIR, typename C> __device__ __forceinline__ void dft4(C *v) { bfly4<DIR>(v[0], v[1], v[2], v[3]); }
 template <int DIR, typename C> __device__ __forceinline__ void dft2(C *v) { bfly2<DIR>(v[0], v[1]); }
 
-// Radix 16 as 4 x 4: A_q = F_4(x[q + 4j]), A_q[k] *= w_16^{q k}, y[k + 4t] = F_4 over q.
+// Radix 16 as 4 x 4, in place: column DFTs F_4 over x[q + 4j] (q in [4]),
+// weights w_16^{q k}, then row DFTs F_4 over q; output k + 4t.
 template <int DIR, typename C> __device__ __forceinline__ void dft16(C *v) {
     using R = typename real_of<C>::type;
     const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173);
     const R h = R(0.70710678118654752440);
-    C a[16];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        C t0 = v[q], t1 = v[q + 4], t2 = v[q + 8], t3 = v[q + 12];
-        bfly4<DIR>(t0, t1, t2, t3);
-        a[q * 4 + 0] = t0;
-        a[q * 4 + 1] = t1;
-        a[q * 4 + 2] = t2;
-        a[q * 4 + 3] = t3;
-    }
-    // weights w_16^{q k}, q, k in [4]; exponent qk in {0,1,2,3,4,6,9}
+    for (int q = 0; q < 4; ++q) bfly4<DIR>(v[q], v[q + 4], v[q + 8], v[q + 12]);
+    // v[q + 4k] now holds column q, frequency k; multiply by w_16^{q k}
     const C w1 = mk<C>(c1, DIR * s1), w2 = mk<C>(h, DIR * h), w3 = mk<C>(s1, DIR * c1);
     const C w6 = mk<C>(-h, DIR * h), w9 = mk<C>(-c1, -DIR * s1);
-    a[1 * 4 + 1] = cmul(a[1 * 4 + 1], w1);
-    a[1 * 4 + 2] = cmul(a[1 * 4 + 2], w2);
-    a[1 * 4 + 3] = cmul(a[1 * 4 + 3], w3);
-    a[2 * 4 + 1] = cmul(a[2 * 4 + 1], w2);
-    a[2 * 4 + 2] = mul_w4<DIR>(a[2 * 4 + 2]);
-    a[2 * 4 + 3] = cmul(a[2 * 4 + 3], w6);
-    a[3 * 4 + 1] = cmul(a[3 * 4 + 1], w3);
-    a[3 * 4 + 2] = cmul(a[3 * 4 + 2], w6);
-    a[3 * 4 + 3] = cmul(a[3 * 4 + 3], w9);
+    v[1 + 4 * 1] = cmul(v[1 + 4 * 1], w1);
+    v[1 + 4 * 2] = cmul(v[1 + 4 * 2], w2);
+    v[1 + 4 * 3] = cmul(v[1 + 4 * 3], w3);
+    v[2 + 4 * 1] = cmul(v[2 + 4 * 1], w2);
+    v[2 + 4 * 2] = mul_w4<DIR>(v[2 + 4 * 2]);
+    v[2 + 4 * 3] = cmul(v[2 + 4 * 3], w6);
+    v[3 + 4 * 1] = cmul(v[3 + 4 * 1], w3);
+    v[3 + 4 * 2] = cmul(v[3 + 4 * 2], w6);
+    v[3 + 4 * 3] = cmul(v[3 + 4 * 3], w9);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        C t0 = a[0 * 4 + k], t1 = a[1 * 4 + k], t2 = a[2 * 4 + k], t3 = a[3 * 4 + k];
-        bfly4<DIR>(t0, t1, t2, t3);
-        v[k] = t0;
-        v[k + 4] = t1;
-        v[k + 8] = t2;
-        v[k + 12] = t3;
-    }
+    for (int k = 0; k < 4; ++k) bfly4<DIR>(v[0 + 4 * k], v[1 + 4 * k], v[2 + 4 * k], v[3 + 4 * k]);
+    // v[t + 4k] holds output k + 4t: transpose the 4 x 4 block (register renaming)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int t = k + 1; t < 4; ++t) {
+            C tmp = v[t + 4 * k];
+            v[t + 4 * k] = v[k + 4 * t];
+            v[k + 4 * t] = tmp;
+        }
 }
 
 template <int R, int DIR, typename C> __device__ __forceinline__ void dft_small(C *v) {

@@ -42,13 +42,14 @@ namespace fftu {
 
 namespace {
 
-template <int N2_, int P2_, int R1_, int B_, int A_, int L0_, int Q1_, int W_>
+template <int N2_, int P2_, int R1_, int B_, int A_, int L0_, int Q1_, int W_, int MINB_>
 struct Cfg {
     static constexpr int N2 = N2_, P2 = P2_, L2 = N2 / P2, R1 = R1_, R2 = L2 / R1;
     static constexpr int B = B_, A = A_, L1 = A * B;
     static constexpr int L0 = L0_, Q1 = Q1_, Q2 = L0 / Q1;
     static constexpr int W = W_, NCH = N2 / W;
-    static constexpr int NT = 512;
+    static constexpr int NT = 256;
+    static constexpr int MINB = MINB_;          // resident CTAs per SM the register budget targets
     static constexpr int TILE1 = B * N2;        // stage-1 elements
     static constexpr int TILE2 = L0 * A * W;    // stage-2 elements
     static constexpr int TILE = TILE1 > TILE2 ? TILE1 : TILE2;
@@ -57,6 +58,7 @@ struct Cfg {
     static constexpr int S2_TASKS = B * NCH;    // stage-2 tasks per unit
     // shared swizzle widths (8-byte words per 128-byte wavefront = 16)
     static constexpr int SW1 = (16 / P2) < R2 ? (16 / P2) : R2;
+    static constexpr int SW2 = (16 / W) < Q2 ? (16 / W) : Q2;
 };
 
 // Run-time geometry shared by every task.
@@ -97,11 +99,28 @@ __device__ bool wait_counter(const unsigned *ctr, unsigned target, long long lim
 
 template <int DIR> __device__ __forceinline__ float2 tw_at(const float2 *t, int e) { return dirw<DIR>(t[e]); }
 
+// Two adjacent complex64 values moved as one 16-byte access.
+struct Pair {
+    float2 a, b;
+};
+__device__ __forceinline__ Pair unpack(float4 v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
+__device__ __forceinline__ float4 pack(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ Pair ld_stream(const float2 *p) { return unpack(__ldcs(reinterpret_cast<const float4 *>(p))); }
+__device__ __forceinline__ Pair ld_l2(const float2 *p) { return unpack(__ldcg(reinterpret_cast<const float4 *>(p))); }
+__device__ __forceinline__ Pair ld_sh(const float2 *p) { return unpack(*reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ void st_sh(float2 *p, float2 a, float2 b) { *reinterpret_cast<float4 *>(p) = pack(a, b); }
+__device__ __forceinline__ void st_stream(float2 *p, float2 a, float2 b) {
+    __stcs(reinterpret_cast<float4 *>(p), pack(a, b));
+}
+__device__ __forceinline__ void st_l2(float2 *p, float2 a, float2 b) { *reinterpret_cast<float4 *>(p) = pack(a, b); }
+
 // ---- stage 1 ----------------------------------------------------------------------------------
-// sm: TILE1 elements.  Shared layouts:
+// sm: TILE1 elements.  Every work item carries two adjacent elements (a pair).
+// Shared layouts:
 //   X1[b][u][q'][s2] with q' = q ^ (u mod SW1)        (exchange inside each row FFT)
-//   X2[b][i2''] with i2'' = L2 s2 + (k2 ^ sigma(s2))    (Put order, swizzled)
-template <class K, int DIR>
+//   X2[b][i2''] with i2'' = L2 s2 + (k2 ^ sigma(s2))    (Put order, swizzled; sigma is even so
+//                                                       pairs of adjacent k2 stay adjacent)
+template <class K>
 __device__ __forceinline__ int x2_index(int b, int k2, int s2) {
     constexpr int sig = 16 / K::P2 > 1 ? 16 / K::P2 : 1;
     const int sw = (s2 * sig) & (K::L2 - 1) & 15;
@@ -109,44 +128,51 @@ __device__ __forceinline__ int x2_index(int b, int k2, int s2) {
 }
 
 template <class K, int DIR>
-__device__ void stage1_task(const Geo &g, float2 *sm, const float2 *s_tw0, const float2 *s_tw1,
-                            const float2 *s_tw2, int s0, int s1, int m0, int a, float2 *dst_unit) {
+__device__ void stage1_task(const Geo &g, float2 *sm, const float2 *s_tw1, const float2 *s_tw2, int s0, int s1,
+                            int m0, int a, float2 *dst_unit) {
     const int tid = threadIdx.x;
-    const int i0 = s0 + g.P0 * m0;
-    const float2 *plane = g.in + (size_t)i0 * g.n1 * K::N2;
-    // S1a: items (b, s2, q), s2 fastest; inputs j = q + R2 r -> i2 = s2 + P2 q + (N2 / R1) r
-    constexpr int IA = K::B * K::P2 * K::R2;
-    static_assert(IA % K::NT == 0 || K::NT % IA == 0, "stage-1a items");
+    constexpr int HP2 = K::P2 / 2;
+    const float2 *plane = g.in + (size_t)(s0 + g.P0 * m0) * g.n1 * K::N2;
+    // S1a: items (b, s2 pair, q), pair fastest; inputs j = q + R2 r -> i2 = s2 + P2 q + (N2 / R1) r;
+    // F_{R1} over r -> u; twiddle w_{L2}^{q u}
+    constexpr int IA = K::B * HP2 * K::R2;
     for (int it = tid; it < IA; it += K::NT) {
-        const int s2 = it % K::P2, q = (it / K::P2) % K::R2, b = it / (K::P2 * K::R2);
-        const int i1 = s1 + g.P1 * (a + K::A * b);
-        const float2 *row = plane + (size_t)i1 * K::N2;
-        float2 v[K::R1];
+        const int sp = it % HP2, q = (it / HP2) % K::R2, b = it / (HP2 * K::R2);
+        const float2 *src = plane + (size_t)(s1 + g.P1 * (a + K::A * b)) * K::N2 + 2 * sp + K::P2 * q;
+        float2 va[K::R1], vb[K::R1];
 #pragma unroll
-        for (int r = 0; r < K::R1; ++r) v[r] = __ldcs(row + s2 + K::P2 * q + (K::N2 / K::R1) * r);
-        dft_small<K::R1, DIR>(v);
+        for (int r = 0; r < K::R1; ++r) {
+            const Pair pr = ld_stream(src + (K::N2 / K::R1) * r);
+            va[r] = pr.a;
+            vb[r] = pr.b;
+        }
+        dft_small<K::R1, DIR>(va);
+        dft_small<K::R1, DIR>(vb);
 #pragma unroll
         for (int u = 0; u < K::R1; ++u) {
-            float2 x = v[u];
-            if (u != 0 && q != 0) x = cmul(x, tw_at<DIR>(s_tw2, (q * u * K::P2) & (K::N2 - 1)));
-            const int qq = q ^ (u % K::SW1);
-            sm[((b * K::R1 + u) * K::R2 + qq) * K::P2 + s2] = x;
+            const float2 w = tw_at<DIR>(s_tw2, (q * u * K::P2) & (K::N2 - 1));
+            st_sh(sm + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp, cmul(va[u], w),
+                  cmul(vb[u], w));
         }
     }
     __syncthreads();
-    // S1b: items (b, s2, u), s2 fastest; F_{R2} over q -> v; k2 = u + R1 v
-    constexpr int IB = K::B * K::P2 * K::R1;
+    // S1b: items (b, s2 pair, u); F_{R2} over q -> v; k2 = u + R1 v; twiddle w_{n2}^{k2 s2}; Put order
+    constexpr int IB = K::B * HP2 * K::R1;
     constexpr int NB = (IB + K::NT - 1) / K::NT;
-    float2 hold[NB][K::R2];
+    float2 ha[NB][K::R2], hb[NB][K::R2];
 #pragma unroll
     for (int h = 0; h < NB; ++h) {
         const int it = tid + h * K::NT;
         if (it < IB) {
-            const int s2 = it % K::P2, u = (it / K::P2) % K::R1, b = it / (K::P2 * K::R1);
+            const int sp = it % HP2, u = (it / HP2) % K::R1, b = it / (HP2 * K::R1);
 #pragma unroll
-            for (int q = 0; q < K::R2; ++q)
-                hold[h][q] = sm[((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + s2];
-            dft_small<K::R2, DIR>(hold[h]);
+            for (int q = 0; q < K::R2; ++q) {
+                const Pair pr = ld_sh(sm + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp);
+                ha[h][q] = pr.a;
+                hb[h][q] = pr.b;
+            }
+            dft_small<K::R2, DIR>(ha[h]);
+            dft_small<K::R2, DIR>(hb[h]);
         }
     }
     __syncthreads();
@@ -154,74 +180,88 @@ __device__ void stage1_task(const Geo &g, float2 *sm, const float2 *s_tw0, const
     for (int h = 0; h < NB; ++h) {
         const int it = tid + h * K::NT;
         if (it < IB) {
-            const int s2 = it % K::P2, u = (it / K::P2) % K::R1, b = it / (K::P2 * K::R1);
+            const int sp = it % HP2, u = (it / HP2) % K::R1, b = it / (HP2 * K::R1);
+            const int s2 = 2 * sp;
 #pragma unroll
             for (int vv = 0; vv < K::R2; ++vv) {
                 const int k2 = u + K::R1 * vv;
-                float2 x = hold[h][vv];
-                if (k2 != 0 && s2 != 0) x = cmul(x, tw_at<DIR>(s_tw2, k2 * s2));
-                sm[x2_index<K, DIR>(b, k2, s2)] = x;
+                sm[x2_index<K>(b, k2, s2)] = cmul(ha[h][vv], tw_at<DIR>(s_tw2, k2 * s2));
+                sm[x2_index<K>(b, k2, s2 + 1)] = cmul(hb[h][vv], tw_at<DIR>(s_tw2, k2 * (s2 + 1)));
             }
         }
     }
     __syncthreads();
-    // S1c: items i2' (Put order); F_B over b -> c; twiddle w_{L1}^{a c}; store to scratch
-    for (int ip = tid; ip < K::N2; ip += K::NT) {
+    // S1c: items (pair of adjacent i2' in Put order); F_B over b -> c; twiddle w_{L1}^{a c}; to scratch
+    constexpr int IC = K::N2 / 2;
+    for (int it = tid; it < IC; it += K::NT) {
+        const int ip = 2 * it;
         const int s2 = ip / K::L2, k2 = ip % K::L2;
-        float2 v[K::B];
+        float2 va[K::B], vb[K::B];
 #pragma unroll
-        for (int b = 0; b < K::B; ++b) v[b] = sm[x2_index<K, DIR>(b, k2, s2)];
-        dft_small<K::B, DIR>(v);
+        for (int b = 0; b < K::B; ++b) {
+            const Pair pr = ld_sh(sm + x2_index<K>(b, k2, s2));
+            va[b] = pr.a;
+            vb[b] = pr.b;
+        }
+        dft_small<K::B, DIR>(va);
+        dft_small<K::B, DIR>(vb);
         const int chunk = ip / K::W, w = ip % K::W;
         float2 *d = dst_unit + (((size_t)chunk * K::L0 + m0) * K::A + a) * K::W + w;
 #pragma unroll
         for (int c = 0; c < K::B; ++c) {
-            float2 x = v[c];
-            if (a != 0 && c != 0) x = cmul(x, tw_at<DIR>(s_tw1, (a * c * g.P1) & (g.n1 - 1)));
-            d[(size_t)c * K::NCH * K::L0 * K::A * K::W] = x;
+            const float2 t = tw_at<DIR>(s_tw1, (a * c * g.P1) & (g.n1 - 1));
+            st_l2(d + (size_t)c * K::NCH * K::L0 * K::A * K::W, cmul(va[c], t), cmul(vb[c], t));
         }
     }
 }
 
 // ---- stage 2 ----------------------------------------------------------------------------------
-// sm: TILE2 elements.  Shared layouts: Y1[e][m0][w]; Y2[e][u'][q'][w].
+// sm: TILE2 elements; items carry pairs of adjacent w.
+// Shared layouts: Y1[e][m0][w]; Y2[e][u'][q''][w] with q'' = q' ^ (u' mod SW2).
 template <class K, int DIR, bool CG>
-__device__ void stage2_task(const Geo &g, float2 *sm, const float2 *s_tw0, const float2 *s_tw1,
-                            const float2 *s_tw2, int s0, int s1, int c, int chunk, const float2 *src_unit) {
+__device__ void stage2_task(const Geo &g, float2 *sm, const float2 *s_tw0, const float2 *s_tw1, int s0, int s1,
+                            int c, int chunk, const float2 *src_unit) {
     const int tid = threadIdx.x;
+    constexpr int HW = K::W / 2;
     const float2 *blk = src_unit + ((size_t)c * K::NCH + chunk) * K::L0 * K::A * K::W;
-    // S2a: items (m0, w), w fastest; F_A over a -> e; k1 = c + B e; twiddle w_{n1}^{k1 s1}
-    constexpr int IA = K::L0 * K::W;
+    // S2a: items (m0, w pair); F_A over a -> e; k1 = c + B e; twiddle w_{n1}^{k1 s1}
+    constexpr int IA = K::L0 * HW;
     for (int it = tid; it < IA; it += K::NT) {
-        const int w = it % K::W, m0 = it / K::W;
-        float2 v[K::A];
+        const int wp = it % HW, m0 = it / HW;
+        float2 va[K::A], vb[K::A];
 #pragma unroll
         for (int a = 0; a < K::A; ++a) {
-            const float2 *p = blk + ((size_t)m0 * K::A + a) * K::W + w;
-            v[a] = CG ? __ldcg(p) : __ldcs(p);
+            const float2 *pa = blk + ((size_t)m0 * K::A + a) * K::W + 2 * wp;
+            const Pair pr = CG ? ld_l2(pa) : ld_stream(pa);
+            va[a] = pr.a;
+            vb[a] = pr.b;
         }
-        dft_small<K::A, DIR>(v);
+        dft_small<K::A, DIR>(va);
+        dft_small<K::A, DIR>(vb);
 #pragma unroll
         for (int e = 0; e < K::A; ++e) {
-            const int k1 = c + K::B * e;
-            float2 x = v[e];
-            if (k1 != 0 && s1 != 0) x = cmul(x, tw_at<DIR>(s_tw1, (k1 * s1) & (g.n1 - 1)));
-            sm[(e * K::L0 + m0) * K::W + w] = x;
+            const float2 t = tw_at<DIR>(s_tw1, ((c + K::B * e) * s1) & (g.n1 - 1));
+            st_sh(sm + (e * K::L0 + m0) * K::W + 2 * wp, cmul(va[e], t), cmul(vb[e], t));
         }
     }
     __syncthreads();
-    // S2b: items (e, q', w), w fastest; m0 = q' + Q2 r; F_{Q1} over r -> u'; twiddle w_{L0}^{q' u'}
-    constexpr int IB = K::A * K::Q2 * K::W;
+    // S2b: items (e, q', w pair); m0 = q' + Q2 r; F_{Q1} over r -> u'; twiddle w_{L0}^{q' u'}
+    constexpr int IB = K::A * K::Q2 * HW;
     constexpr int NB = (IB + K::NT - 1) / K::NT;
-    float2 hold[NB][K::Q1];
+    float2 ha[NB][K::Q1], hb[NB][K::Q1];
 #pragma unroll
     for (int h = 0; h < NB; ++h) {
         const int it = tid + h * K::NT;
         if (it < IB) {
-            const int w = it % K::W, q = (it / K::W) % K::Q2, e = it / (K::W * K::Q2);
+            const int wp = it % HW, q = (it / HW) % K::Q2, e = it / (HW * K::Q2);
 #pragma unroll
-            for (int r = 0; r < K::Q1; ++r) hold[h][r] = sm[(e * K::L0 + q + K::Q2 * r) * K::W + w];
-            dft_small<K::Q1, DIR>(hold[h]);
+            for (int r = 0; r < K::Q1; ++r) {
+                const Pair pr = ld_sh(sm + (e * K::L0 + q + K::Q2 * r) * K::W + 2 * wp);
+                ha[h][r] = pr.a;
+                hb[h][r] = pr.b;
+            }
+            dft_small<K::Q1, DIR>(ha[h]);
+            dft_small<K::Q1, DIR>(hb[h]);
         }
     }
     __syncthreads();
@@ -229,32 +269,35 @@ __device__ void stage2_task(const Geo &g, float2 *sm, const float2 *s_tw0, const
     for (int h = 0; h < NB; ++h) {
         const int it = tid + h * K::NT;
         if (it < IB) {
-            const int w = it % K::W, q = (it / K::W) % K::Q2, e = it / (K::W * K::Q2);
+            const int wp = it % HW, q = (it / HW) % K::Q2, e = it / (HW * K::Q2);
 #pragma unroll
             for (int u = 0; u < K::Q1; ++u) {
-                float2 x = hold[h][u];
-                if (u != 0 && q != 0) x = cmul(x, tw_at<DIR>(s_tw0, (q * u * g.P0) & (g.n0 - 1)));
-                sm[((e * K::Q1 + u) * K::Q2 + q) * K::W + w] = x;
+                const float2 t = tw_at<DIR>(s_tw0, (q * u * g.P0) & (g.n0 - 1));
+                st_sh(sm + ((e * K::Q1 + u) * K::Q2 + (q ^ (u % K::SW2))) * K::W + 2 * wp, cmul(ha[h][u], t),
+                      cmul(hb[h][u], t));
             }
         }
     }
     __syncthreads();
-    // S2c: items (e, u', w), w fastest; F_{Q2} over q' -> v'; k0 = u' + Q1 v'; twiddle w_{n0}^{k0 s0}
-    constexpr int IC = K::A * K::Q1 * K::W;
+    // S2c: items (e, u', w pair); F_{Q2} over q' -> v'; k0 = u' + Q1 v'; twiddle w_{n0}^{k0 s0}; store
+    constexpr int IC = K::A * K::Q1 * HW;
     for (int it = tid; it < IC; it += K::NT) {
-        const int w = it % K::W, u = (it / K::W) % K::Q1, e = it / (K::W * K::Q1);
-        float2 v[K::Q2];
+        const int wp = it % HW, u = (it / HW) % K::Q1, e = it / (HW * K::Q1);
+        float2 va[K::Q2], vb[K::Q2];
 #pragma unroll
-        for (int q = 0; q < K::Q2; ++q) v[q] = sm[((e * K::Q1 + u) * K::Q2 + q) * K::W + w];
-        dft_small<K::Q2, DIR>(v);
-        const int k1 = c + K::B * e;
-        float2 *dst = g.out + ((size_t)(k1 + K::L1 * s1) * K::N2 + (size_t)chunk * K::W + w);
+        for (int q = 0; q < K::Q2; ++q) {
+            const Pair pr = ld_sh(sm + ((e * K::Q1 + u) * K::Q2 + (q ^ (u % K::SW2))) * K::W + 2 * wp);
+            va[q] = pr.a;
+            vb[q] = pr.b;
+        }
+        dft_small<K::Q2, DIR>(va);
+        dft_small<K::Q2, DIR>(vb);
+        float2 *dst = g.out + ((size_t)(c + K::B * e + K::L1 * s1) * K::N2 + (size_t)chunk * K::W + 2 * wp);
 #pragma unroll
         for (int vv = 0; vv < K::Q2; ++vv) {
             const int k0 = u + K::Q1 * vv;
-            float2 x = v[vv];
-            if (k0 != 0 && s0 != 0) x = cmul(x, tw_at<DIR>(s_tw0, (k0 * s0) & (g.n0 - 1)));
-            __stcs(dst + (size_t)(k0 + K::L0 * s0) * g.n1 * K::N2, x);
+            const float2 t = tw_at<DIR>(s_tw0, (k0 * s0) & (g.n0 - 1));
+            st_stream(dst + (size_t)(k0 + K::L0 * s0) * g.n1 * K::N2, cmul(va[vv], t), cmul(vb[vv], t));
         }
     }
 }
@@ -269,7 +312,7 @@ __device__ void load_tables(const Geo &g, float2 *s_tw0, float2 *s_tw1, float2 *
 
 // Shared memory: tables (n0 + n1 + N2 entries) then the tile.
 template <class K, int DIR>
-__global__ void __launch_bounds__(K::NT, 2) stage1_kernel(const __grid_constant__ Geo g) {
+__global__ void __launch_bounds__(K::NT, K::MINB) stage1_kernel(const __grid_constant__ Geo g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *s_tw0 = reinterpret_cast<float2 *>(smem_raw);
     float2 *s_tw1 = s_tw0 + g.n0, *s_tw2 = s_tw1 + g.n1, *sm = s_tw2 + K::N2;
@@ -279,13 +322,13 @@ __global__ void __launch_bounds__(K::NT, 2) stage1_kernel(const __grid_constant_
         const int unit = t / K::S1_TASKS, lt = t % K::S1_TASKS;
         const int s0 = unit / g.P1, s1 = unit % g.P1;
         const int m0 = lt / K::A, a = lt % K::A;
-        stage1_task<K, DIR>(g, sm, s_tw0, s_tw1, s_tw2, s0, s1, m0, a, g.scratch + (size_t)unit * K::UNIT);
+        stage1_task<K, DIR>(g, sm, s_tw1, s_tw2, s0, s1, m0, a, g.scratch + (size_t)unit * K::UNIT);
         __syncthreads();
     }
 }
 
 template <class K, int DIR>
-__global__ void __launch_bounds__(K::NT, 2) stage2_kernel(const __grid_constant__ Geo g) {
+__global__ void __launch_bounds__(K::NT, K::MINB) stage2_kernel(const __grid_constant__ Geo g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *s_tw0 = reinterpret_cast<float2 *>(smem_raw);
     float2 *s_tw1 = s_tw0 + g.n0, *s_tw2 = s_tw1 + g.n1, *sm = s_tw2 + K::N2;
@@ -295,15 +338,14 @@ __global__ void __launch_bounds__(K::NT, 2) stage2_kernel(const __grid_constant_
         const int unit = t / K::S2_TASKS, lt = t % K::S2_TASKS;
         const int s0 = unit / g.P1, s1 = unit % g.P1;
         const int c = lt / K::NCH, chunk = lt % K::NCH;
-        stage2_task<K, DIR, false>(g, sm, s_tw0, s_tw1, s_tw2, s0, s1, c, chunk,
-                                   g.scratch + (size_t)unit * K::UNIT);
+        stage2_task<K, DIR, false>(g, sm, s_tw0, s_tw1, s0, s1, c, chunk, g.scratch + (size_t)unit * K::UNIT);
         __syncthreads();
     }
 }
 
 // Persistent ring kernel.  Task order: S1(0), S1(1), S2(0), S1(2), S2(1), ..., S2(U-1).
 template <class K, int DIR>
-__global__ void __launch_bounds__(K::NT, 2) ring_kernel(const __grid_constant__ Geo g) {
+__global__ void __launch_bounds__(K::NT, K::MINB) ring_kernel(const __grid_constant__ Geo g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *s_tw0 = reinterpret_cast<float2 *>(smem_raw);
     float2 *s_tw1 = s_tw0 + g.n0, *s_tw2 = s_tw1 + g.n1, *sm = s_tw2 + K::N2;
@@ -354,9 +396,9 @@ __global__ void __launch_bounds__(K::NT, 2) ring_kernel(const __grid_constant__ 
         __syncthreads();
         if (s_ok) {
             if (is_s1) {
-                stage1_task<K, DIR>(g, sm, s_tw0, s_tw1, s_tw2, s0, s1, lt / K::A, lt % K::A, slot);
+                stage1_task<K, DIR>(g, sm, s_tw1, s_tw2, s0, s1, lt / K::A, lt % K::A, slot);
             } else {
-                stage2_task<K, DIR, true>(g, sm, s_tw0, s_tw1, s_tw2, s0, s1, lt / K::NCH, lt % K::NCH, slot);
+                stage2_task<K, DIR, true>(g, sm, s_tw0, s_tw1, s0, s1, lt / K::NCH, lt % K::NCH, slot);
             }
         }
         __syncthreads();
@@ -436,10 +478,10 @@ cudaError_t prepare_k(int n0, int n1, int *grids) {
 }
 
 // Instantiated configurations (complex64):
-//   512^3, p = 8^3: L = 64, rows 64 = 8 x 8, axis 1 = 8 x 8, axis 0 = 8 x 8, W = 16
-//   512^3, p = 4^3: L = 128, rows 128 = 16 x 8, axis 1 = 8 x 16, axis 0 = 16 x 8, W = 8
-using K512p8 = Cfg<512, 8, 8, 8, 8, 64, 8, 16>;
-using K512p4 = Cfg<512, 4, 16, 16, 8, 128, 16, 8>;
+//   512^3, p = 8^3: L = 64, rows 64 = 8 x 8, axis 1 = 8 x 8, axis 0 = 8 x 8, W = 8; 3 CTAs/SM
+//   512^3, p = 4^3: L = 128, rows 128 = 8 x 16, axis 1 = 16 x 8, axis 0 = 8 x 16, W = 4; 2 CTAs/SM
+using K512p8 = Cfg<512, 8, 8, 8, 8, 64, 8, 8, 3>;
+using K512p4 = Cfg<512, 4, 8, 8, 16, 128, 8, 4, 2>;
 
 template <int DIR, bool PREP>
 cudaError_t dispatch(int which, const Phase3Launch *l, cudaStream_t st, int n0, int n1, int *grid, size_t *smem) {
