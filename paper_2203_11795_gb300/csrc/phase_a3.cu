@@ -99,6 +99,67 @@ __device__ bool wait_counter(const unsigned *ctr, unsigned target, long long lim
 
 template <int DIR> __device__ __forceinline__ float2 tw_at(const float2 *t, int e) { return dirw<DIR>(t[e]); }
 
+// Per-CTA twiddle tables in shared memory, already conjugated for the inverse
+// and laid out so that the lanes of a warp read consecutive entries (or one
+// broadcast entry) in every pass.
+struct Tabs {
+    float4 *tb;  // [k2][s2 / 2]: (w_{n2}^{k2 s2}, w_{n2}^{k2 (s2 + 1)})        stage 1b
+    float2 *ta;  // [u][q]: w_{L2}^{q u}                                         stage 1a
+    float2 *td;  // [u'][q']: w_{L0}^{q' u'}                                     stage 2b
+    float2 *t1;  // [e]: w_{n1}^e (read as a broadcast)                          stages 1c, 2a
+    float2 *te;  // [s0][k0]: w_{n0}^{k0 s0}                                     stage 2c
+    float2 *tile;
+};
+
+template <class K>
+__host__ __device__ constexpr size_t table_elems(int n0, int n1) {
+    return (size_t)K::L2 * K::P2 + K::R1 * K::R2 + K::Q1 * K::Q2 + n1 + n0;
+}
+
+template <class K, int DIR>
+__device__ __forceinline__ Tabs build_tables(const Geo &g, unsigned char *raw) {
+    Tabs T;
+    T.tile = reinterpret_cast<float2 *>(raw);
+    T.tb = reinterpret_cast<float4 *>(T.tile + K::TILE);
+    T.ta = reinterpret_cast<float2 *>(T.tb + K::L2 * K::P2 / 2);
+    T.td = T.ta + K::R1 * K::R2;
+    T.t1 = T.td + K::Q1 * K::Q2;
+    T.te = T.t1 + g.n1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < K::L2 * K::P2 / 2; i += nt) {
+        const int k2 = i / (K::P2 / 2), s2 = 2 * (i % (K::P2 / 2));
+        const float2 w0 = tw_at<DIR>(g.tw2, k2 * s2), w1 = tw_at<DIR>(g.tw2, k2 * (s2 + 1));
+        T.tb[i] = make_float4(w0.x, w0.y, w1.x, w1.y);
+    }
+    for (int i = tid; i < K::R1 * K::R2; i += nt)
+        T.ta[i] = tw_at<DIR>(g.tw2, ((i % K::R2) * (i / K::R2) * K::P2) & (K::N2 - 1));
+    for (int i = tid; i < K::Q1 * K::Q2; i += nt)
+        T.td[i] = tw_at<DIR>(g.tw0, ((i % K::Q2) * (i / K::Q2) * g.P0) & (g.n0 - 1));
+    for (int i = tid; i < g.n1; i += nt) T.t1[i] = tw_at<DIR>(g.tw1, i);
+    for (int i = tid; i < g.n0; i += nt) {
+        const int s0 = i / K::L0, k0 = i % K::L0;
+        T.te[i] = tw_at<DIR>(g.tw0, (k0 * s0) & (g.n0 - 1));
+    }
+    __syncthreads();
+    return T;
+}
+
+// Scratch stores of the ring keep their lines in L2 (evict-last policy); the
+// stage-2 reader discards them after use so dead lines are never written back.
+__device__ __forceinline__ unsigned long long l2_keep_policy() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void st_keep(float2 *p, float2 a, float2 b, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(a.x), "f"(a.y),
+                 "f"(b.x), "f"(b.y), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void discard_l2_line(const void *p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 // Two adjacent complex64 values moved as one 16-byte access.
 struct Pair {
     float2 a, b;
@@ -127,10 +188,10 @@ __device__ __forceinline__ int x2_index(int b, int k2, int s2) {
     return b * K::N2 + K::L2 * s2 + (k2 ^ sw);
 }
 
-template <class K, int DIR>
-__device__ void stage1_task(const Geo &g, float2 *sm, const float2 *s_tw1, const float2 *s_tw2, int s0, int s1,
-                            int m0, int a, float2 *dst_unit) {
+template <class K, int DIR, bool RING>
+__device__ __forceinline__ void stage1_task(const Geo &g, const Tabs &T, int s0, int s1, int m0, int a, float2 *dst_unit) {
     const int tid = threadIdx.x;
+    float2 *sm = T.tile;
     constexpr int HP2 = K::P2 / 2;
     const float2 *plane = g.in + (size_t)(s0 + g.P0 * m0) * g.n1 * K::N2;
     // S1a: items (b, s2 pair, q), pair fastest; inputs j = q + R2 r -> i2 = s2 + P2 q + (N2 / R1) r;
@@ -150,7 +211,7 @@ __device__ void stage1_task(const Geo &g, float2 *sm, const float2 *s_tw1, const
         dft_small<K::R1, DIR>(vb);
 #pragma unroll
         for (int u = 0; u < K::R1; ++u) {
-            const float2 w = tw_at<DIR>(s_tw2, (q * u * K::P2) & (K::N2 - 1));
+            const float2 w = T.ta[u * K::R2 + q];
             st_sh(sm + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp, cmul(va[u], w),
                   cmul(vb[u], w));
         }
@@ -185,8 +246,9 @@ __device__ void stage1_task(const Geo &g, float2 *sm, const float2 *s_tw1, const
 #pragma unroll
             for (int vv = 0; vv < K::R2; ++vv) {
                 const int k2 = u + K::R1 * vv;
-                sm[x2_index<K>(b, k2, s2)] = cmul(ha[h][vv], tw_at<DIR>(s_tw2, k2 * s2));
-                sm[x2_index<K>(b, k2, s2 + 1)] = cmul(hb[h][vv], tw_at<DIR>(s_tw2, k2 * (s2 + 1)));
+                const float4 tt = T.tb[k2 * HP2 + sp];
+                sm[x2_index<K>(b, k2, s2)] = cmul(ha[h][vv], make_float2(tt.x, tt.y));
+                sm[x2_index<K>(b, k2, s2 + 1)] = cmul(hb[h][vv], make_float2(tt.z, tt.w));
             }
         }
     }
@@ -207,10 +269,16 @@ __device__ void stage1_task(const Geo &g, float2 *sm, const float2 *s_tw1, const
         dft_small<K::B, DIR>(vb);
         const int chunk = ip / K::W, w = ip % K::W;
         float2 *d = dst_unit + (((size_t)chunk * K::L0 + m0) * K::A + a) * K::W + w;
+        unsigned long long pol = 0;
+        if constexpr (RING) pol = l2_keep_policy();
 #pragma unroll
         for (int c = 0; c < K::B; ++c) {
-            const float2 t = tw_at<DIR>(s_tw1, (a * c * g.P1) & (g.n1 - 1));
-            st_l2(d + (size_t)c * K::NCH * K::L0 * K::A * K::W, cmul(va[c], t), cmul(vb[c], t));
+            const float2 t = T.t1[(a * c * g.P1) & (g.n1 - 1)];
+            float2 *dc = d + (size_t)c * K::NCH * K::L0 * K::A * K::W;
+            if constexpr (RING)
+                st_keep(dc, cmul(va[c], t), cmul(vb[c], t), pol);
+            else
+                st_l2(dc, cmul(va[c], t), cmul(vb[c], t));
         }
     }
 }
@@ -218,10 +286,10 @@ __device__ void stage1_task(const Geo &g, float2 *sm, const float2 *s_tw1, const
 // ---- stage 2 ----------------------------------------------------------------------------------
 // sm: TILE2 elements; items carry pairs of adjacent w.
 // Shared layouts: Y1[e][m0][w]; Y2[e][u'][q''][w] with q'' = q' ^ (u' mod SW2).
-template <class K, int DIR, bool CG>
-__device__ void stage2_task(const Geo &g, float2 *sm, const float2 *s_tw0, const float2 *s_tw1, int s0, int s1,
-                            int c, int chunk, const float2 *src_unit) {
+template <class K, int DIR, bool RING>
+__device__ __forceinline__ void stage2_task(const Geo &g, const Tabs &T, int s0, int s1, int c, int chunk, const float2 *src_unit) {
     const int tid = threadIdx.x;
+    float2 *sm = T.tile;
     constexpr int HW = K::W / 2;
     const float2 *blk = src_unit + ((size_t)c * K::NCH + chunk) * K::L0 * K::A * K::W;
     // S2a: items (m0, w pair); F_A over a -> e; k1 = c + B e; twiddle w_{n1}^{k1 s1}
@@ -232,7 +300,7 @@ __device__ void stage2_task(const Geo &g, float2 *sm, const float2 *s_tw0, const
 #pragma unroll
         for (int a = 0; a < K::A; ++a) {
             const float2 *pa = blk + ((size_t)m0 * K::A + a) * K::W + 2 * wp;
-            const Pair pr = CG ? ld_l2(pa) : ld_stream(pa);
+            const Pair pr = RING ? ld_l2(pa) : ld_stream(pa);
             va[a] = pr.a;
             vb[a] = pr.b;
         }
@@ -240,11 +308,16 @@ __device__ void stage2_task(const Geo &g, float2 *sm, const float2 *s_tw0, const
         dft_small<K::A, DIR>(vb);
 #pragma unroll
         for (int e = 0; e < K::A; ++e) {
-            const float2 t = tw_at<DIR>(s_tw1, ((c + K::B * e) * s1) & (g.n1 - 1));
+            const float2 t = T.t1[((c + K::B * e) * s1) & (g.n1 - 1)];
             st_sh(sm + (e * K::L0 + m0) * K::W + 2 * wp, cmul(va[e], t), cmul(vb[e], t));
         }
     }
     __syncthreads();
+    if constexpr (RING) {
+        // the block is dead once in shared memory: drop its L2 lines without write-back
+        constexpr int LINES = K::L0 * K::A * K::W * (int)sizeof(float2) / 128;
+        for (int i = tid; i < LINES; i += K::NT) discard_l2_line(reinterpret_cast<const char *>(blk) + 128 * i);
+    }
     // S2b: items (e, q', w pair); m0 = q' + Q2 r; F_{Q1} over r -> u'; twiddle w_{L0}^{q' u'}
     constexpr int IB = K::A * K::Q2 * HW;
     constexpr int NB = (IB + K::NT - 1) / K::NT;
@@ -272,7 +345,7 @@ __device__ void stage2_task(const Geo &g, float2 *sm, const float2 *s_tw0, const
             const int wp = it % HW, q = (it / HW) % K::Q2, e = it / (HW * K::Q2);
 #pragma unroll
             for (int u = 0; u < K::Q1; ++u) {
-                const float2 t = tw_at<DIR>(s_tw0, (q * u * g.P0) & (g.n0 - 1));
+                const float2 t = T.td[u * K::Q2 + q];
                 st_sh(sm + ((e * K::Q1 + u) * K::Q2 + (q ^ (u % K::SW2))) * K::W + 2 * wp, cmul(ha[h][u], t),
                       cmul(hb[h][u], t));
             }
@@ -296,33 +369,23 @@ __device__ void stage2_task(const Geo &g, float2 *sm, const float2 *s_tw0, const
 #pragma unroll
         for (int vv = 0; vv < K::Q2; ++vv) {
             const int k0 = u + K::Q1 * vv;
-            const float2 t = tw_at<DIR>(s_tw0, (k0 * s0) & (g.n0 - 1));
+            const float2 t = T.te[s0 * K::L0 + k0];
             st_stream(dst + (size_t)(k0 + K::L0 * s0) * g.n1 * K::N2, cmul(va[vv], t), cmul(vb[vv], t));
         }
     }
-}
-
-template <class K>
-__device__ void load_tables(const Geo &g, float2 *s_tw0, float2 *s_tw1, float2 *s_tw2) {
-    for (int e = threadIdx.x; e < g.n0; e += blockDim.x) s_tw0[e] = g.tw0[e];
-    for (int e = threadIdx.x; e < g.n1; e += blockDim.x) s_tw1[e] = g.tw1[e];
-    for (int e = threadIdx.x; e < K::N2; e += blockDim.x) s_tw2[e] = g.tw2[e];
-    __syncthreads();
 }
 
 // Shared memory: tables (n0 + n1 + N2 entries) then the tile.
 template <class K, int DIR>
 __global__ void __launch_bounds__(K::NT, K::MINB) stage1_kernel(const __grid_constant__ Geo g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *s_tw0 = reinterpret_cast<float2 *>(smem_raw);
-    float2 *s_tw1 = s_tw0 + g.n0, *s_tw2 = s_tw1 + g.n1, *sm = s_tw2 + K::N2;
-    load_tables<K>(g, s_tw0, s_tw1, s_tw2);
+    const Tabs T = build_tables<K, DIR>(g, smem_raw);
     const int total = g.units * K::S1_TASKS;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int unit = t / K::S1_TASKS, lt = t % K::S1_TASKS;
         const int s0 = unit / g.P1, s1 = unit % g.P1;
         const int m0 = lt / K::A, a = lt % K::A;
-        stage1_task<K, DIR>(g, sm, s_tw1, s_tw2, s0, s1, m0, a, g.scratch + (size_t)unit * K::UNIT);
+        stage1_task<K, DIR, false>(g, T, s0, s1, m0, a, g.scratch + (size_t)unit * K::UNIT);
         __syncthreads();
     }
 }
@@ -330,15 +393,13 @@ __global__ void __launch_bounds__(K::NT, K::MINB) stage1_kernel(const __grid_con
 template <class K, int DIR>
 __global__ void __launch_bounds__(K::NT, K::MINB) stage2_kernel(const __grid_constant__ Geo g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *s_tw0 = reinterpret_cast<float2 *>(smem_raw);
-    float2 *s_tw1 = s_tw0 + g.n0, *s_tw2 = s_tw1 + g.n1, *sm = s_tw2 + K::N2;
-    load_tables<K>(g, s_tw0, s_tw1, s_tw2);
+    const Tabs T = build_tables<K, DIR>(g, smem_raw);
     const int total = g.units * K::S2_TASKS;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int unit = t / K::S2_TASKS, lt = t % K::S2_TASKS;
         const int s0 = unit / g.P1, s1 = unit % g.P1;
         const int c = lt / K::NCH, chunk = lt % K::NCH;
-        stage2_task<K, DIR, false>(g, sm, s_tw0, s_tw1, s0, s1, c, chunk, g.scratch + (size_t)unit * K::UNIT);
+        stage2_task<K, DIR, false>(g, T, s0, s1, c, chunk, g.scratch + (size_t)unit * K::UNIT);
         __syncthreads();
     }
 }
@@ -347,11 +408,9 @@ __global__ void __launch_bounds__(K::NT, K::MINB) stage2_kernel(const __grid_con
 template <class K, int DIR>
 __global__ void __launch_bounds__(K::NT, K::MINB) ring_kernel(const __grid_constant__ Geo g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *s_tw0 = reinterpret_cast<float2 *>(smem_raw);
-    float2 *s_tw1 = s_tw0 + g.n0, *s_tw2 = s_tw1 + g.n1, *sm = s_tw2 + K::N2;
     __shared__ int s_task;
     __shared__ int s_ok;
-    load_tables<K>(g, s_tw0, s_tw1, s_tw2);
+    const Tabs T = build_tables<K, DIR>(g, smem_raw);
     const int U = g.units;
     const int total = U * (K::S1_TASKS + K::S2_TASKS);
     unsigned *task_ctr = g.counters;
@@ -396,9 +455,9 @@ __global__ void __launch_bounds__(K::NT, K::MINB) ring_kernel(const __grid_const
         __syncthreads();
         if (s_ok) {
             if (is_s1) {
-                stage1_task<K, DIR>(g, sm, s_tw1, s_tw2, s0, s1, lt / K::A, lt % K::A, slot);
+                stage1_task<K, DIR, true>(g, T, s0, s1, lt / K::A, lt % K::A, slot);
             } else {
-                stage2_task<K, DIR, true>(g, sm, s_tw0, s_tw1, s0, s1, lt / K::NCH, lt % K::NCH, slot);
+                stage2_task<K, DIR, true>(g, T, s0, s1, lt / K::NCH, lt % K::NCH, slot);
             }
         }
         __syncthreads();
@@ -413,7 +472,7 @@ __global__ void __launch_bounds__(K::NT, K::MINB) ring_kernel(const __grid_const
 
 template <class K>
 size_t smem_bytes(int n0, int n1) {
-    return (size_t)(n0 + n1 + K::N2 + K::TILE) * sizeof(float2);
+    return (table_elems<K>(n0, n1) + K::TILE) * sizeof(float2);
 }
 
 template <class K, int DIR>
