@@ -59,6 +59,8 @@ struct Cfg {
     // shared swizzle widths (8-byte words per 128-byte wavefront = 16)
     static constexpr int SW1 = (16 / P2) < R2 ? (16 / P2) : R2;
     static constexpr int SW2 = (16 / W) < Q2 ? (16 / W) : Q2;
+    static constexpr int SWA = ((16 / W) < A ? (16 / W) : A) - 1;  // scratch row swizzle mask
+    static constexpr int NS = 2;                 // shared input buffers (pipeline depth)
 };
 
 // Run-time geometry shared by every task.
@@ -119,8 +121,8 @@ __host__ __device__ constexpr size_t table_elems(int n0, int n1) {
 template <class K, int DIR>
 __device__ __forceinline__ Tabs build_tables(const Geo &g, unsigned char *raw) {
     Tabs T;
-    T.tile = reinterpret_cast<float2 *>(raw);
-    T.tb = reinterpret_cast<float4 *>(T.tile + K::TILE);
+    T.tile = nullptr;
+    T.tb = reinterpret_cast<float4 *>(raw);
     T.ta = reinterpret_cast<float2 *>(T.tb + K::L2 * K::P2 / 2);
     T.td = T.ta + K::R1 * K::R2;
     T.t1 = T.td + K::Q1 * K::Q2;
@@ -166,8 +168,6 @@ struct Pair {
 };
 __device__ __forceinline__ Pair unpack(float4 v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
 __device__ __forceinline__ float4 pack(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
-__device__ __forceinline__ Pair ld_stream(const float2 *p) { return unpack(__ldcs(reinterpret_cast<const float4 *>(p))); }
-__device__ __forceinline__ Pair ld_l2(const float2 *p) { return unpack(__ldcg(reinterpret_cast<const float4 *>(p))); }
 __device__ __forceinline__ Pair ld_sh(const float2 *p) { return unpack(*reinterpret_cast<const float4 *>(p)); }
 __device__ __forceinline__ void st_sh(float2 *p, float2 a, float2 b) { *reinterpret_cast<float4 *>(p) = pack(a, b); }
 __device__ __forceinline__ void st_stream(float2 *p, float2 a, float2 b) {
@@ -175,12 +175,55 @@ __device__ __forceinline__ void st_stream(float2 *p, float2 a, float2 b) {
 }
 __device__ __forceinline__ void st_l2(float2 *p, float2 a, float2 b) { *reinterpret_cast<float4 *>(p) = pack(a, b); }
 
-// ---- stage 1 ----------------------------------------------------------------------------------
-// sm: TILE1 elements.  Every work item carries two adjacent elements (a pair).
-// Shared layouts:
+// ---- pipeline primitives: mbarriers and bulk copies ----------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false when the budget runs out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long limit_ns) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try(bar, parity))
+        if ((long long)(global_ns() - t0) > limit_ns) return false;
+    return true;
+}
+// One-dimensional bulk copy global -> shared, completing on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Order this thread's earlier generic-proxy acquires before its later bulk-copy reads of global memory.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory"); }
+
+// ---- stage 1: compute on a landed tile of B rows ------------------------------------------------
+// buf: the B rows of the task, natural order [b][i2] as the bulk copies left them.
+// In place, shared layouts after the first exchange:
 //   X1[b][u][q'][s2] with q' = q ^ (u mod SW1)        (exchange inside each row FFT)
 //   X2[b][i2''] with i2'' = L2 s2 + (k2 ^ sigma(s2))    (Put order, swizzled; sigma is even so
 //                                                       pairs of adjacent k2 stay adjacent)
+// Output: the scratch block of unit `dst_unit`, element (c, i2', m0, a) at
+//   block (c, i2' / W), row m0 * A + (a ^ (m0 & SWA)), column i2' % W
+// (the row swizzle makes the stage-2 reads of the landed block conflict-free).
 template <class K>
 __device__ __forceinline__ int x2_index(int b, int k2, int s2) {
     constexpr int sig = 16 / K::P2 > 1 ? 16 / K::P2 : 1;
@@ -189,92 +232,107 @@ __device__ __forceinline__ int x2_index(int b, int k2, int s2) {
 }
 
 template <class K, int DIR, bool RING>
-__device__ __forceinline__ void stage1_task(const Geo &g, const Tabs &T, int s0, int s1, int m0, int a, float2 *dst_unit) {
+__device__ __forceinline__ void stage1_compute(const Geo &g, const Tabs &T, float2 *buf, int m0, int a,
+                                               float2 *dst_unit) {
     const int tid = threadIdx.x;
-    float2 *sm = T.tile;
     constexpr int HP2 = K::P2 / 2;
-    const float2 *plane = g.in + (size_t)(s0 + g.P0 * m0) * g.n1 * K::N2;
-    // S1a: items (b, s2 pair, q), pair fastest; inputs j = q + R2 r -> i2 = s2 + P2 q + (N2 / R1) r;
+    // S1a: items (b, s2 pair, q); inputs j = q + R2 r -> i2 = s2 + P2 q + (N2 / R1) r;
     // F_{R1} over r -> u; twiddle w_{L2}^{q u}
     constexpr int IA = K::B * HP2 * K::R2;
-    for (int it = tid; it < IA; it += K::NT) {
-        const int sp = it % HP2, q = (it / HP2) % K::R2, b = it / (HP2 * K::R2);
-        const float2 *src = plane + (size_t)(s1 + g.P1 * (a + K::A * b)) * K::N2 + 2 * sp + K::P2 * q;
-        float2 va[K::R1], vb[K::R1];
+    constexpr int NA = (IA + K::NT - 1) / K::NT;
+    {
+        float2 ha[NA][K::R1], hb[NA][K::R1];
 #pragma unroll
-        for (int r = 0; r < K::R1; ++r) {
-            const Pair pr = ld_stream(src + (K::N2 / K::R1) * r);
-            va[r] = pr.a;
-            vb[r] = pr.b;
-        }
-        dft_small<K::R1, DIR>(va);
-        dft_small<K::R1, DIR>(vb);
+        for (int h = 0; h < NA; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IA) {
+                const int sp = it % HP2, q = (it / HP2) % K::R2, b = it / (HP2 * K::R2);
 #pragma unroll
-        for (int u = 0; u < K::R1; ++u) {
-            const float2 w = T.ta[u * K::R2 + q];
-            st_sh(sm + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp, cmul(va[u], w),
-                  cmul(vb[u], w));
+                for (int r = 0; r < K::R1; ++r) {
+                    const Pair pr = ld_sh(buf + b * K::N2 + 2 * sp + K::P2 * q + (K::N2 / K::R1) * r);
+                    ha[h][r] = pr.a;
+                    hb[h][r] = pr.b;
+                }
+                dft_small<K::R1, DIR>(ha[h]);
+                dft_small<K::R1, DIR>(hb[h]);
+            }
         }
+        consumer_sync<K::NT>();
+#pragma unroll
+        for (int h = 0; h < NA; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IA) {
+                const int sp = it % HP2, q = (it / HP2) % K::R2, b = it / (HP2 * K::R2);
+#pragma unroll
+                for (int u = 0; u < K::R1; ++u) {
+                    const float2 w = T.ta[u * K::R2 + q];
+                    st_sh(buf + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp, cmul(ha[h][u], w),
+                          cmul(hb[h][u], w));
+                }
+            }
+        }
+        consumer_sync<K::NT>();
     }
-    __syncthreads();
     // S1b: items (b, s2 pair, u); F_{R2} over q -> v; k2 = u + R1 v; twiddle w_{n2}^{k2 s2}; Put order
     constexpr int IB = K::B * HP2 * K::R1;
     constexpr int NB = (IB + K::NT - 1) / K::NT;
-    float2 ha[NB][K::R2], hb[NB][K::R2];
+    {
+        float2 ha[NB][K::R2], hb[NB][K::R2];
 #pragma unroll
-    for (int h = 0; h < NB; ++h) {
-        const int it = tid + h * K::NT;
-        if (it < IB) {
-            const int sp = it % HP2, u = (it / HP2) % K::R1, b = it / (HP2 * K::R1);
+        for (int h = 0; h < NB; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IB) {
+                const int sp = it % HP2, u = (it / HP2) % K::R1, b = it / (HP2 * K::R1);
 #pragma unroll
-            for (int q = 0; q < K::R2; ++q) {
-                const Pair pr = ld_sh(sm + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp);
-                ha[h][q] = pr.a;
-                hb[h][q] = pr.b;
-            }
-            dft_small<K::R2, DIR>(ha[h]);
-            dft_small<K::R2, DIR>(hb[h]);
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int h = 0; h < NB; ++h) {
-        const int it = tid + h * K::NT;
-        if (it < IB) {
-            const int sp = it % HP2, u = (it / HP2) % K::R1, b = it / (HP2 * K::R1);
-            const int s2 = 2 * sp;
-#pragma unroll
-            for (int vv = 0; vv < K::R2; ++vv) {
-                const int k2 = u + K::R1 * vv;
-                const float4 tt = T.tb[k2 * HP2 + sp];
-                sm[x2_index<K>(b, k2, s2)] = cmul(ha[h][vv], make_float2(tt.x, tt.y));
-                sm[x2_index<K>(b, k2, s2 + 1)] = cmul(hb[h][vv], make_float2(tt.z, tt.w));
+                for (int q = 0; q < K::R2; ++q) {
+                    const Pair pr = ld_sh(buf + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp);
+                    ha[h][q] = pr.a;
+                    hb[h][q] = pr.b;
+                }
+                dft_small<K::R2, DIR>(ha[h]);
+                dft_small<K::R2, DIR>(hb[h]);
             }
         }
+        consumer_sync<K::NT>();
+#pragma unroll
+        for (int h = 0; h < NB; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IB) {
+                const int sp = it % HP2, u = (it / HP2) % K::R1, b = it / (HP2 * K::R1);
+                const int s2 = 2 * sp;
+#pragma unroll
+                for (int vv = 0; vv < K::R2; ++vv) {
+                    const int k2 = u + K::R1 * vv;
+                    const float4 tt = T.tb[k2 * HP2 + sp];
+                    buf[x2_index<K>(b, k2, s2)] = cmul(ha[h][vv], make_float2(tt.x, tt.y));
+                    buf[x2_index<K>(b, k2, s2 + 1)] = cmul(hb[h][vv], make_float2(tt.z, tt.w));
+                }
+            }
+        }
+        consumer_sync<K::NT>();
     }
-    __syncthreads();
     // S1c: items (pair of adjacent i2' in Put order); F_B over b -> c; twiddle w_{L1}^{a c}; to scratch
     constexpr int IC = K::N2 / 2;
+    const int arow = m0 * K::A + (a ^ (m0 & K::SWA));
+    unsigned long long pol = 0;
+    if constexpr (RING) pol = l2_keep_policy();
     for (int it = tid; it < IC; it += K::NT) {
         const int ip = 2 * it;
         const int s2 = ip / K::L2, k2 = ip % K::L2;
         float2 va[K::B], vb[K::B];
 #pragma unroll
         for (int b = 0; b < K::B; ++b) {
-            const Pair pr = ld_sh(sm + x2_index<K>(b, k2, s2));
+            const Pair pr = ld_sh(buf + x2_index<K>(b, k2, s2));
             va[b] = pr.a;
             vb[b] = pr.b;
         }
         dft_small<K::B, DIR>(va);
         dft_small<K::B, DIR>(vb);
-        const int chunk = ip / K::W, w = ip % K::W;
-        float2 *d = dst_unit + (((size_t)chunk * K::L0 + m0) * K::A + a) * K::W + w;
-        unsigned long long pol = 0;
-        if constexpr (RING) pol = l2_keep_policy();
+        float2 *d = dst_unit + (size_t)(ip / K::W) * K::TILE2 + arow * K::W + ip % K::W;
 #pragma unroll
         for (int c = 0; c < K::B; ++c) {
             const float2 t = T.t1[(a * c * g.P1) & (g.n1 - 1)];
-            float2 *dc = d + (size_t)c * K::NCH * K::L0 * K::A * K::W;
+            float2 *dc = d + (size_t)c * K::NCH * K::TILE2;
             if constexpr (RING)
                 st_keep(dc, cmul(va[c], t), cmul(vb[c], t), pol);
             else
@@ -283,75 +341,85 @@ __device__ __forceinline__ void stage1_task(const Geo &g, const Tabs &T, int s0,
     }
 }
 
-// ---- stage 2 ----------------------------------------------------------------------------------
-// sm: TILE2 elements; items carry pairs of adjacent w.
-// Shared layouts: Y1[e][m0][w]; Y2[e][u'][q''][w] with q'' = q' ^ (u' mod SW2).
-template <class K, int DIR, bool RING>
-__device__ __forceinline__ void stage2_task(const Geo &g, const Tabs &T, int s0, int s1, int c, int chunk, const float2 *src_unit) {
+// ---- stage 2: compute on a landed block --------------------------------------------------------
+// buf: the L0 x A x W block of one (c, chunk), rows swizzled as stage 1 wrote them.
+// In place, shared layouts: Y1[e][m0][w]; Y2[e][u'][q''][w] with q'' = q' ^ (u' mod SW2).
+template <class K, int DIR>
+__device__ __forceinline__ void stage2_compute(const Geo &g, const Tabs &T, float2 *buf, int s0, int s1, int c,
+                                               int chunk) {
     const int tid = threadIdx.x;
-    float2 *sm = T.tile;
     constexpr int HW = K::W / 2;
-    const float2 *blk = src_unit + ((size_t)c * K::NCH + chunk) * K::L0 * K::A * K::W;
     // S2a: items (m0, w pair); F_A over a -> e; k1 = c + B e; twiddle w_{n1}^{k1 s1}
     constexpr int IA = K::L0 * HW;
-    for (int it = tid; it < IA; it += K::NT) {
-        const int wp = it % HW, m0 = it / HW;
-        float2 va[K::A], vb[K::A];
+    constexpr int NA = (IA + K::NT - 1) / K::NT;
+    {
+        float2 ha[NA][K::A], hb[NA][K::A];
 #pragma unroll
-        for (int a = 0; a < K::A; ++a) {
-            const float2 *pa = blk + ((size_t)m0 * K::A + a) * K::W + 2 * wp;
-            const Pair pr = RING ? ld_l2(pa) : ld_stream(pa);
-            va[a] = pr.a;
-            vb[a] = pr.b;
-        }
-        dft_small<K::A, DIR>(va);
-        dft_small<K::A, DIR>(vb);
+        for (int h = 0; h < NA; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IA) {
+                const int wp = it % HW, m0 = it / HW;
 #pragma unroll
-        for (int e = 0; e < K::A; ++e) {
-            const float2 t = T.t1[((c + K::B * e) * s1) & (g.n1 - 1)];
-            st_sh(sm + (e * K::L0 + m0) * K::W + 2 * wp, cmul(va[e], t), cmul(vb[e], t));
+                for (int a = 0; a < K::A; ++a) {
+                    const Pair pr = ld_sh(buf + (m0 * K::A + (a ^ (m0 & K::SWA))) * K::W + 2 * wp);
+                    ha[h][a] = pr.a;
+                    hb[h][a] = pr.b;
+                }
+                dft_small<K::A, DIR>(ha[h]);
+                dft_small<K::A, DIR>(hb[h]);
+            }
         }
-    }
-    __syncthreads();
-    if constexpr (RING) {
-        // the block is dead once in shared memory: drop its L2 lines without write-back
-        constexpr int LINES = K::L0 * K::A * K::W * (int)sizeof(float2) / 128;
-        for (int i = tid; i < LINES; i += K::NT) discard_l2_line(reinterpret_cast<const char *>(blk) + 128 * i);
+        consumer_sync<K::NT>();
+#pragma unroll
+        for (int h = 0; h < NA; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IA) {
+                const int wp = it % HW, m0 = it / HW;
+#pragma unroll
+                for (int e = 0; e < K::A; ++e) {
+                    const float2 t = T.t1[((c + K::B * e) * s1) & (g.n1 - 1)];
+                    st_sh(buf + (e * K::L0 + m0) * K::W + 2 * wp, cmul(ha[h][e], t), cmul(hb[h][e], t));
+                }
+            }
+        }
+        consumer_sync<K::NT>();
     }
     // S2b: items (e, q', w pair); m0 = q' + Q2 r; F_{Q1} over r -> u'; twiddle w_{L0}^{q' u'}
     constexpr int IB = K::A * K::Q2 * HW;
     constexpr int NB = (IB + K::NT - 1) / K::NT;
-    float2 ha[NB][K::Q1], hb[NB][K::Q1];
+    {
+        float2 ha[NB][K::Q1], hb[NB][K::Q1];
 #pragma unroll
-    for (int h = 0; h < NB; ++h) {
-        const int it = tid + h * K::NT;
-        if (it < IB) {
-            const int wp = it % HW, q = (it / HW) % K::Q2, e = it / (HW * K::Q2);
+        for (int h = 0; h < NB; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IB) {
+                const int wp = it % HW, q = (it / HW) % K::Q2, e = it / (HW * K::Q2);
 #pragma unroll
-            for (int r = 0; r < K::Q1; ++r) {
-                const Pair pr = ld_sh(sm + (e * K::L0 + q + K::Q2 * r) * K::W + 2 * wp);
-                ha[h][r] = pr.a;
-                hb[h][r] = pr.b;
-            }
-            dft_small<K::Q1, DIR>(ha[h]);
-            dft_small<K::Q1, DIR>(hb[h]);
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int h = 0; h < NB; ++h) {
-        const int it = tid + h * K::NT;
-        if (it < IB) {
-            const int wp = it % HW, q = (it / HW) % K::Q2, e = it / (HW * K::Q2);
-#pragma unroll
-            for (int u = 0; u < K::Q1; ++u) {
-                const float2 t = T.td[u * K::Q2 + q];
-                st_sh(sm + ((e * K::Q1 + u) * K::Q2 + (q ^ (u % K::SW2))) * K::W + 2 * wp, cmul(ha[h][u], t),
-                      cmul(hb[h][u], t));
+                for (int r = 0; r < K::Q1; ++r) {
+                    const Pair pr = ld_sh(buf + (e * K::L0 + q + K::Q2 * r) * K::W + 2 * wp);
+                    ha[h][r] = pr.a;
+                    hb[h][r] = pr.b;
+                }
+                dft_small<K::Q1, DIR>(ha[h]);
+                dft_small<K::Q1, DIR>(hb[h]);
             }
         }
+        consumer_sync<K::NT>();
+#pragma unroll
+        for (int h = 0; h < NB; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IB) {
+                const int wp = it % HW, q = (it / HW) % K::Q2, e = it / (HW * K::Q2);
+#pragma unroll
+                for (int u = 0; u < K::Q1; ++u) {
+                    const float2 t = T.td[u * K::Q2 + q];
+                    st_sh(buf + ((e * K::Q1 + u) * K::Q2 + (q ^ (u % K::SW2))) * K::W + 2 * wp, cmul(ha[h][u], t),
+                          cmul(hb[h][u], t));
+                }
+            }
+        }
+        consumer_sync<K::NT>();
     }
-    __syncthreads();
     // S2c: items (e, u', w pair); F_{Q2} over q' -> v'; k0 = u' + Q1 v'; twiddle w_{n0}^{k0 s0}; store
     constexpr int IC = K::A * K::Q1 * HW;
     for (int it = tid; it < IC; it += K::NT) {
@@ -359,7 +427,7 @@ __device__ __forceinline__ void stage2_task(const Geo &g, const Tabs &T, int s0,
         float2 va[K::Q2], vb[K::Q2];
 #pragma unroll
         for (int q = 0; q < K::Q2; ++q) {
-            const Pair pr = ld_sh(sm + ((e * K::Q1 + u) * K::Q2 + (q ^ (u % K::SW2))) * K::W + 2 * wp);
+            const Pair pr = ld_sh(buf + ((e * K::Q1 + u) * K::Q2 + (q ^ (u % K::SW2))) * K::W + 2 * wp);
             va[q] = pr.a;
             vb[q] = pr.b;
         }
@@ -375,105 +443,167 @@ __device__ __forceinline__ void stage2_task(const Geo &g, const Tabs &T, int s0,
     }
 }
 
-// Shared memory: tables (n0 + n1 + N2 entries) then the tile.
-template <class K, int DIR>
-__global__ void __launch_bounds__(K::NT, K::MINB) stage1_kernel(const __grid_constant__ Geo g) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Tabs T = build_tables<K, DIR>(g, smem_raw);
-    const int total = g.units * K::S1_TASKS;
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        const int unit = t / K::S1_TASKS, lt = t % K::S1_TASKS;
-        const int s0 = unit / g.P1, s1 = unit % g.P1;
-        const int m0 = lt / K::A, a = lt % K::A;
-        stage1_task<K, DIR, false>(g, T, s0, s1, m0, a, g.scratch + (size_t)unit * K::UNIT);
-        __syncthreads();
+// ---- the pipelined kernel --------------------------------------------------------------------------
+// MODE 0: stage 1 of every task (two-kernel schedule, scratch = workspace of N elements)
+// MODE 1: stage 2 of every task (two-kernel schedule)
+// MODE 2: persistent ring, task order S1(0), S1(1), S2(0), S1(2), S2(1), ..., S2(U-1)
+//
+// Warp roles: NT consumer threads compute; one producer warp (lane 0) takes tasks, waits for their
+// dependencies (ring), and lands each task's input in one of NS shared buffers with bulk copies
+// (B rows of N2 elements for stage 1, one contiguous block for stage 2), completing the buffer's
+// `full` mbarrier.  Consumers release a buffer through its `empty` mbarrier.
+template <class K>
+__device__ __forceinline__ void decode_task(int t, int U, int mode, int &unit, int &lt, int &is_s1) {
+    if (mode == 0) {
+        unit = t / K::S1_TASKS;
+        lt = t % K::S1_TASKS;
+        is_s1 = 1;
+    } else if (mode == 1) {
+        unit = t / K::S2_TASKS;
+        lt = t % K::S2_TASKS;
+        is_s1 = 0;
+    } else if (t < K::S1_TASKS) {
+        unit = 0;
+        lt = t;
+        is_s1 = 1;
+    } else {
+        const int r = t - K::S1_TASKS;
+        const int grp = K::S1_TASKS + K::S2_TASKS;
+        const int j = r / grp + 1, o = r % grp;
+        if (j < U && o < K::S1_TASKS) {
+            unit = j;
+            lt = o;
+            is_s1 = 1;
+        } else {
+            unit = j - 1;
+            lt = j < U ? o - K::S1_TASKS : o;
+            is_s1 = 0;
+        }
     }
 }
 
-template <class K, int DIR>
-__global__ void __launch_bounds__(K::NT, K::MINB) stage2_kernel(const __grid_constant__ Geo g) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Tabs T = build_tables<K, DIR>(g, smem_raw);
-    const int total = g.units * K::S2_TASKS;
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        const int unit = t / K::S2_TASKS, lt = t % K::S2_TASKS;
-        const int s0 = unit / g.P1, s1 = unit % g.P1;
-        const int c = lt / K::NCH, chunk = lt % K::NCH;
-        stage2_task<K, DIR, false>(g, T, s0, s1, c, chunk, g.scratch + (size_t)unit * K::UNIT);
-        __syncthreads();
-    }
+template <class K>
+__host__ __device__ constexpr size_t pipe_smem_bytes(int n0, int n1) {
+    return (size_t)K::NS * K::TILE * sizeof(float2) + table_elems<K>(n0, n1) * sizeof(float2) +
+           2 * K::NS * sizeof(uint64_t) + K::NS * sizeof(int) + 16;
 }
 
-// Persistent ring kernel.  Task order: S1(0), S1(1), S2(0), S1(2), S2(1), ..., S2(U-1).
-template <class K, int DIR>
-__global__ void __launch_bounds__(K::NT, K::MINB) ring_kernel(const __grid_constant__ Geo g) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_task;
-    __shared__ int s_ok;
-    const Tabs T = build_tables<K, DIR>(g, smem_raw);
+template <class K, int DIR, int MODE>
+__global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_constant__ Geo g) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2 *bufs = reinterpret_cast<float2 *>(smem_raw);
+    const Tabs T = build_tables<K, DIR>(g, smem_raw + (size_t)K::NS * K::TILE * sizeof(float2));
+    uint64_t *full = reinterpret_cast<uint64_t *>(
+        (reinterpret_cast<uintptr_t>(T.te + g.n0) + 7) & ~static_cast<uintptr_t>(7));
+    uint64_t *empty = full + K::NS;
+    int *task = reinterpret_cast<int *>(empty + K::NS);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < K::NS; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
     const int U = g.units;
-    const int total = U * (K::S1_TASKS + K::S2_TASKS);
+    const int total = MODE == 0 ? U * K::S1_TASKS : MODE == 1 ? U * K::S2_TASKS : U * (K::S1_TASKS + K::S2_TASKS);
     unsigned *task_ctr = g.counters;
     unsigned *s1_done = g.counters + 1;
     unsigned *s2_done = g.counters + 1 + U;
-    for (;;) {
-        if (threadIdx.x == 0) s_task = (int)atomicAdd(task_ctr, 1u);
-        __syncthreads();
-        const int t = s_task;
-        if (t >= total) break;
-        // decode: group 0 = S1(0); group j >= 1 = S1(j) (if j < U) followed by S2(j - 1)
+
+    if (threadIdx.x >= K::NT) {
+        // ---------------- producer ----------------
+        if (threadIdx.x != K::NT) return;
+        for (int i = 0;; ++i) {
+            const int s = i % K::NS;
+            const unsigned ph = (unsigned)(i / K::NS) & 1u;
+            if (i >= K::NS && !mbar_wait(empty + s, ph ^ 1u, g.spin_limit)) {
+                atomicCAS(g.status, 0, (int)FFTU_ERR_TIMEOUT);
+                task[s] = -1;
+                mbar_arrive(full + s);
+                break;
+            }
+            const int t = MODE == 2 ? (int)atomicAdd(task_ctr, 1u) : (int)blockIdx.x + i * (int)gridDim.x;
+            if (t >= total) {
+                task[s] = -1;
+                mbar_arrive(full + s);
+                break;
+            }
+            int unit, lt, is_s1;
+            decode_task<K>(t, U, MODE, unit, lt, is_s1);
+            if (MODE == 2) {
+                bool ok = true;
+                if (is_s1) {
+                    if (unit >= g.ring) ok = wait_counter(s2_done + (unit - g.ring), K::S2_TASKS, g.spin_limit, g.status);
+                } else {
+                    ok = wait_counter(s1_done + unit, K::S1_TASKS, g.spin_limit, g.status);
+                }
+                if (!ok) {
+                    task[s] = -1;
+                    mbar_arrive(full + s);
+                    break;
+                }
+                fence_proxy_async_global();
+            }
+            task[s] = t;
+            float2 *dst = bufs + (size_t)s * K::TILE;
+            const int s0 = unit / g.P1, s1 = unit % g.P1;
+            if (is_s1) {
+                const int m0 = lt / K::A, a = lt % K::A;
+                const float2 *plane = g.in + (size_t)(s0 + g.P0 * m0) * g.n1 * K::N2;
+                mbar_arrive_tx(full + s, K::B * K::N2 * (unsigned)sizeof(float2));
+#pragma unroll 1
+                for (int b = 0; b < K::B; ++b)
+                    bulk_g2s(dst + b * K::N2, plane + (size_t)(s1 + g.P1 * (a + K::A * b)) * K::N2,
+                             K::N2 * (unsigned)sizeof(float2), full + s);
+            } else {
+                const float2 *slot = g.scratch + (size_t)(MODE == 2 ? unit % g.ring : unit) * K::UNIT;
+                mbar_arrive_tx(full + s, K::TILE2 * (unsigned)sizeof(float2));
+                bulk_g2s(dst, slot + (size_t)lt * K::TILE2, K::TILE2 * (unsigned)sizeof(float2), full + s);
+            }
+        }
+        return;
+    }
+    // ---------------- consumers ----------------
+    for (int i = 0;; ++i) {
+        const int s = i % K::NS;
+        const unsigned ph = (unsigned)(i / K::NS) & 1u;
+        if (!mbar_wait(full + s, ph, g.spin_limit)) {
+            if (threadIdx.x == 0) atomicCAS(g.status, 0, (int)FFTU_ERR_TIMEOUT);
+            break;
+        }
+        const int t = task[s];
+        if (t < 0) break;
         int unit, lt, is_s1;
-        if (t < K::S1_TASKS) {
-            unit = 0;
-            lt = t;
-            is_s1 = 1;
-        } else {
-            const int r = t - K::S1_TASKS;
-            const int grp = K::S1_TASKS + K::S2_TASKS;
-            const int j = r / grp + 1, o = r % grp;
-            if (j < U && o < K::S1_TASKS) {
-                unit = j;
-                lt = o;
-                is_s1 = 1;
-            } else {
-                unit = j - 1;
-                lt = j < U ? o - K::S1_TASKS : o;
-                is_s1 = 0;
-            }
-        }
+        decode_task<K>(t, U, MODE, unit, lt, is_s1);
         const int s0 = unit / g.P1, s1 = unit % g.P1;
-        float2 *slot = g.scratch + (size_t)(unit % g.ring) * K::UNIT;
-        if (threadIdx.x == 0) {
-            bool ok = true;
-            if (is_s1) {
-                if (unit >= g.ring) ok = wait_counter(s2_done + (unit - g.ring), K::S2_TASKS, g.spin_limit, g.status);
-            } else {
-                ok = wait_counter(s1_done + unit, K::S1_TASKS, g.spin_limit, g.status);
-            }
-            s_ok = ok;
-        }
-        __syncthreads();
-        if (s_ok) {
-            if (is_s1) {
-                stage1_task<K, DIR, true>(g, T, s0, s1, lt / K::A, lt % K::A, slot);
-            } else {
-                stage2_task<K, DIR, true>(g, T, s0, s1, lt / K::NCH, lt % K::NCH, slot);
+        float2 *buf = bufs + (size_t)s * K::TILE;
+        if (is_s1) {
+            float2 *slot = g.scratch + (size_t)(MODE == 2 ? unit % g.ring : unit) * K::UNIT;
+            stage1_compute<K, DIR, MODE == 2>(g, T, buf, lt / K::A, lt % K::A, slot);
+        } else {
+            stage2_compute<K, DIR>(g, T, buf, s0, s1, lt / K::NCH, lt % K::NCH);
+            if (MODE == 2) {
+                // the block has been read: drop its L2 lines without write-back
+                const float2 *blk = g.scratch + (size_t)(unit % g.ring) * K::UNIT + (size_t)lt * K::TILE2;
+                constexpr int LINES = K::TILE2 * (int)sizeof(float2) / 128;
+                for (int l = threadIdx.x; l < LINES; l += K::NT)
+                    discard_l2_line(reinterpret_cast<const char *>(blk) + 128 * l);
             }
         }
-        __syncthreads();
+        consumer_sync<K::NT>();
         if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(is_s1 ? s1_done + unit : s2_done + unit, 1u);
+            mbar_arrive(empty + s);
+            if (MODE == 2) {
+                __threadfence();
+                atomicAdd(is_s1 ? s1_done + unit : s2_done + unit, 1u);
+            }
         }
     }
 }
 
 // ---- host side --------------------------------------------------------------------------------
-
-template <class K>
-size_t smem_bytes(int n0, int n1) {
-    return (table_elems<K>(n0, n1) + K::TILE) * sizeof(float2);
-}
 
 template <class K, int DIR>
 cudaError_t launch_k(const Phase3Launch &l, cudaStream_t st) {
@@ -493,20 +623,20 @@ cudaError_t launch_k(const Phase3Launch &l, cudaStream_t st) {
     g.units = l.p0 * l.p1;
     g.ring = l.ring;
     g.spin_limit = l.spin_limit_ns;
-    const size_t smem = smem_bytes<K>(l.n0, l.n1);
+    const size_t smem = pipe_smem_bytes<K>(l.n0, l.n1);
     if (l.mode == 0) {
         int grid1 = g.units * K::S1_TASKS, grid2 = g.units * K::S2_TASKS;
         if (grid1 > l.grid1) grid1 = l.grid1;
         if (grid2 > l.grid2) grid2 = l.grid2;
-        stage1_kernel<K, DIR><<<grid1, K::NT, smem, st>>>(g);
+        pipe_kernel<K, DIR, 0><<<grid1, K::NT + 32, smem, st>>>(g);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        stage2_kernel<K, DIR><<<grid2, K::NT, smem, st>>>(g);
+        pipe_kernel<K, DIR, 1><<<grid2, K::NT + 32, smem, st>>>(g);
         return cudaGetLastError();
     }
     cudaError_t e = cudaMemsetAsync(l.counters, 0, sizeof(unsigned) * (1 + 2 * (size_t)g.units), st);
     if (e != cudaSuccess) return e;
-    ring_kernel<K, DIR><<<l.grid, K::NT, smem, st>>>(g);
+    pipe_kernel<K, DIR, 2><<<l.grid, K::NT + 32, smem, st>>>(g);
     return cudaGetLastError();
 }
 
@@ -529,27 +659,27 @@ cudaError_t setup_kernel(F *fn, int nt, size_t smem, int *grid_out) {
 
 template <class K, int DIR>
 cudaError_t prepare_k(int n0, int n1, int *grids) {
-    const size_t smem = smem_bytes<K>(n0, n1);
-    cudaError_t e = setup_kernel(stage1_kernel<K, DIR>, K::NT, smem, &grids[0]);
-    if (e == cudaSuccess) e = setup_kernel(stage2_kernel<K, DIR>, K::NT, smem, &grids[1]);
-    if (e == cudaSuccess) e = setup_kernel(ring_kernel<K, DIR>, K::NT, smem, &grids[2]);
+    const size_t smem = pipe_smem_bytes<K>(n0, n1);
+    cudaError_t e = setup_kernel(pipe_kernel<K, DIR, 0>, K::NT + 32, smem, &grids[0]);
+    if (e == cudaSuccess) e = setup_kernel(pipe_kernel<K, DIR, 1>, K::NT + 32, smem, &grids[1]);
+    if (e == cudaSuccess) e = setup_kernel(pipe_kernel<K, DIR, 2>, K::NT + 32, smem, &grids[2]);
     return e;
 }
 
 // Instantiated configurations (complex64):
-//   512^3, p = 8^3: L = 64, rows 64 = 8 x 8, axis 1 = 8 x 8, axis 0 = 8 x 8, W = 8; 3 CTAs/SM
-//   512^3, p = 4^3: L = 128, rows 128 = 8 x 16, axis 1 = 16 x 8, axis 0 = 8 x 16, W = 4; 2 CTAs/SM
-using K512p8 = Cfg<512, 8, 8, 8, 8, 64, 8, 8, 3>;
-using K512p4 = Cfg<512, 4, 8, 8, 16, 128, 8, 4, 2>;
+//   512^3, p = 8^3: L = 64, rows 64 = 8 x 8, axis 1 = 8 x 8, axis 0 = 8 x 8, W = 8; 2 CTAs/SM
+//   512^3, p = 4^3: L = 128, rows 128 = 8 x 16, axis 1 = 16 x 8, axis 0 = 8 x 16, W = 4; 1 CTA/SM
+using K512p8 = Cfg<512, 8, 8, 8, 8, 64, 8, 8, 2>;
+using K512p4 = Cfg<512, 4, 8, 8, 16, 128, 8, 4, 1>;
 
 template <int DIR, bool PREP>
 cudaError_t dispatch(int which, const Phase3Launch *l, cudaStream_t st, int n0, int n1, int *grid, size_t *smem) {
     switch (which) {
         case 0:
-            if (smem) *smem = smem_bytes<K512p8>(n0, n1);
+            if (smem) *smem = pipe_smem_bytes<K512p8>(n0, n1);
             return PREP ? prepare_k<K512p8, DIR>(n0, n1, grid) : launch_k<K512p8, DIR>(*l, st);
         case 1:
-            if (smem) *smem = smem_bytes<K512p4>(n0, n1);
+            if (smem) *smem = pipe_smem_bytes<K512p4>(n0, n1);
             return PREP ? prepare_k<K512p4, DIR>(n0, n1, grid) : launch_k<K512p4, DIR>(*l, st);
     }
     return cudaErrorInvalidValue;
