@@ -514,17 +514,41 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
 
     if (threadIdx.x >= K::NT) {
         // ---------------- producer ----------------
+        // Besides landing inputs, the producer publishes task completion for the ring: once the
+        // consumers release a buffer (its `empty` phase completes, which orders every consumer
+        // store of that task before it), a gpu-scope fence and a counter increment make the task's
+        // output visible to the other CTAs.  Completed tasks are also published while the producer
+        // waits on a dependency, so a CTA never waits on its own unpublished work.
         if (threadIdx.x != K::NT) return;
-        for (int i = 0;; ++i) {
+        int pend_task[K::NS];
+        unsigned pend_par[K::NS];
+        for (int s = 0; s < K::NS; ++s) {
+            pend_task[s] = -1;
+            pend_par[s] = 0;
+        }
+        auto publish = [&](int s, bool block) -> bool {
+            if (pend_task[s] < 0) return true;
+            const bool done = block ? mbar_wait(empty + s, pend_par[s], g.spin_limit) : mbar_try(empty + s, pend_par[s]);
+            if (!done) return false;
+            if (MODE == 2) {
+                int unit, lt, is_s1;
+                decode_task<K>(pend_task[s], U, MODE, unit, lt, is_s1);
+                __threadfence();
+                atomicAdd(is_s1 ? s1_done + unit : s2_done + unit, 1u);
+            }
+            pend_task[s] = -1;
+            return true;
+        };
+        bool abort = false;
+        int i = 0;
+        for (;; ++i) {
             const int s = i % K::NS;
             const unsigned ph = (unsigned)(i / K::NS) & 1u;
-            if (i >= K::NS && !mbar_wait(empty + s, ph ^ 1u, g.spin_limit)) {
+            if (i >= K::NS && !publish(s, true)) {  // buffer s free again
                 atomicCAS(g.status, 0, (int)FFTU_ERR_TIMEOUT);
-                task[s] = -1;
-                mbar_arrive(full + s);
-                break;
+                abort = true;
             }
-            const int t = MODE == 2 ? (int)atomicAdd(task_ctr, 1u) : (int)blockIdx.x + i * (int)gridDim.x;
+            const int t = abort ? total : MODE == 2 ? (int)atomicAdd(task_ctr, 1u) : (int)blockIdx.x + i * (int)gridDim.x;
             if (t >= total) {
                 task[s] = -1;
                 mbar_arrive(full + s);
@@ -533,20 +557,40 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
             int unit, lt, is_s1;
             decode_task<K>(t, U, MODE, unit, lt, is_s1);
             if (MODE == 2) {
-                bool ok = true;
-                if (is_s1) {
-                    if (unit >= g.ring) ok = wait_counter(s2_done + (unit - g.ring), K::S2_TASKS, g.spin_limit, g.status);
-                } else {
-                    ok = wait_counter(s1_done + unit, K::S1_TASKS, g.spin_limit, g.status);
+                const unsigned *ctr = nullptr;
+                unsigned target = 0;
+                if (is_s1 && unit >= g.ring) {
+                    ctr = s2_done + (unit - g.ring);
+                    target = K::S2_TASKS;
+                } else if (!is_s1) {
+                    ctr = s1_done + unit;
+                    target = K::S1_TASKS;
                 }
-                if (!ok) {
-                    task[s] = -1;
-                    mbar_arrive(full + s);
-                    break;
+                if (ctr) {
+                    const unsigned long long t0 = global_ns();
+                    for (;;) {
+                        unsigned v;
+                        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+                        if (v >= target) break;
+                        for (int o = 0; o < K::NS; ++o) publish(o, false);
+                        if ((long long)(global_ns() - t0) > g.spin_limit) {
+                            atomicCAS(g.status, 0, (int)FFTU_ERR_TIMEOUT);
+                            abort = true;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                    if (abort) {
+                        task[s] = -1;
+                        mbar_arrive(full + s);
+                        break;
+                    }
                 }
                 fence_proxy_async_global();
             }
             task[s] = t;
+            pend_task[s] = t;
+            pend_par[s] = ph;
             float2 *dst = bufs + (size_t)s * K::TILE;
             const int s0 = unit / g.P1, s1 = unit % g.P1;
             if (is_s1) {
@@ -563,6 +607,9 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
                 bulk_g2s(dst, slot + (size_t)lt * K::TILE2, K::TILE2 * (unsigned)sizeof(float2), full + s);
             }
         }
+        // publish the tasks still in flight (the consumers finish them before seeing the sentinel)
+        for (int s = 0; s < K::NS; ++s)
+            if (!publish(s, true)) atomicCAS(g.status, 0, (int)FFTU_ERR_TIMEOUT);
         return;
     }
     // ---------------- consumers ----------------
@@ -593,13 +640,7 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
             }
         }
         consumer_sync<K::NT>();
-        if (threadIdx.x == 0) {
-            mbar_arrive(empty + s);
-            if (MODE == 2) {
-                __threadfence();
-                atomicAdd(is_s1 ? s1_done + unit : s2_done + unit, 1u);
-            }
-        }
+        if (threadIdx.x == 0) mbar_arrive(empty + s);  // releases the buffer; the producer publishes the task
     }
 }
 
