@@ -84,21 +84,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Bounded wait for counters[idx] >= target (one thread); false on timeout.
-__device__ bool wait_counter(const unsigned *ctr, unsigned target, long long limit_ns, int *status) {
-    const unsigned long long t0 = global_ns();
-    unsigned v;
-    for (;;) {
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
-        if (v >= target) return true;
-        if ((long long)(global_ns() - t0) > limit_ns) {
-            atomicCAS(status, 0, (int)FFTU_ERR_TIMEOUT);
-            return false;
-        }
-        __nanosleep(64);
-    }
-}
-
 template <int DIR> __device__ __forceinline__ float2 tw_at(const float2 *t, int e) { return dirw<DIR>(t[e]); }
 
 // Per-CTA twiddle tables in shared memory, already conjugated for the inverse
@@ -232,86 +217,57 @@ __device__ __forceinline__ int x2_index(int b, int k2, int s2) {
 }
 
 template <class K, int DIR, bool RING>
-__device__ __forceinline__ void stage1_compute(const Geo &g, const Tabs &T, float2 *buf, int m0, int a,
+__device__ __forceinline__ void stage1_compute(const Geo &g, const Tabs &T, float2 *buf, float2 *work, int m0, int a,
                                                float2 *dst_unit) {
     const int tid = threadIdx.x;
     constexpr int HP2 = K::P2 / 2;
-    // S1a: items (b, s2 pair, q); inputs j = q + R2 r -> i2 = s2 + P2 q + (N2 / R1) r;
-    // F_{R1} over r -> u; twiddle w_{L2}^{q u}
+    // S1a (buf -> work): items (b, s2 pair, q); inputs j = q + R2 r -> i2 = s2 + P2 q + (N2 / R1) r;
+    // F_{R1} over r -> u; twiddle w_{L2}^{q u}; X1 layout
     constexpr int IA = K::B * HP2 * K::R2;
-    constexpr int NA = (IA + K::NT - 1) / K::NT;
-    {
-        float2 ha[NA][K::R1], hb[NA][K::R1];
+    for (int it = tid; it < IA; it += K::NT) {
+        const int sp = it % HP2, q = (it / HP2) % K::R2, b = it / (HP2 * K::R2);
+        float2 va[K::R1], vb[K::R1];
 #pragma unroll
-        for (int h = 0; h < NA; ++h) {
-            const int it = tid + h * K::NT;
-            if (it < IA) {
-                const int sp = it % HP2, q = (it / HP2) % K::R2, b = it / (HP2 * K::R2);
-#pragma unroll
-                for (int r = 0; r < K::R1; ++r) {
-                    const Pair pr = ld_sh(buf + b * K::N2 + 2 * sp + K::P2 * q + (K::N2 / K::R1) * r);
-                    ha[h][r] = pr.a;
-                    hb[h][r] = pr.b;
-                }
-                dft_small<K::R1, DIR>(ha[h]);
-                dft_small<K::R1, DIR>(hb[h]);
-            }
+        for (int r = 0; r < K::R1; ++r) {
+            const Pair pr = ld_sh(buf + b * K::N2 + 2 * sp + K::P2 * q + (K::N2 / K::R1) * r);
+            va[r] = pr.a;
+            vb[r] = pr.b;
         }
-        consumer_sync<K::NT>();
+        dft_small<K::R1, DIR>(va);
+        dft_small<K::R1, DIR>(vb);
 #pragma unroll
-        for (int h = 0; h < NA; ++h) {
-            const int it = tid + h * K::NT;
-            if (it < IA) {
-                const int sp = it % HP2, q = (it / HP2) % K::R2, b = it / (HP2 * K::R2);
-#pragma unroll
-                for (int u = 0; u < K::R1; ++u) {
-                    const float2 w = T.ta[u * K::R2 + q];
-                    st_sh(buf + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp, cmul(ha[h][u], w),
-                          cmul(hb[h][u], w));
-                }
-            }
+        for (int u = 0; u < K::R1; ++u) {
+            const float2 w = T.ta[u * K::R2 + q];
+            st_sh(work + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp, cmul(va[u], w),
+                  cmul(vb[u], w));
         }
-        consumer_sync<K::NT>();
     }
-    // S1b: items (b, s2 pair, u); F_{R2} over q -> v; k2 = u + R1 v; twiddle w_{n2}^{k2 s2}; Put order
+    consumer_sync<K::NT>();
+    // S1b (work -> buf): items (b, s2 pair, u); F_{R2} over q -> v; k2 = u + R1 v; twiddle w_{n2}^{k2 s2};
+    // Put order (X2 layout)
     constexpr int IB = K::B * HP2 * K::R1;
-    constexpr int NB = (IB + K::NT - 1) / K::NT;
-    {
-        float2 ha[NB][K::R2], hb[NB][K::R2];
+    for (int it = tid; it < IB; it += K::NT) {
+        const int sp = it % HP2, u = (it / HP2) % K::R1, b = it / (HP2 * K::R1);
+        float2 va[K::R2], vb[K::R2];
 #pragma unroll
-        for (int h = 0; h < NB; ++h) {
-            const int it = tid + h * K::NT;
-            if (it < IB) {
-                const int sp = it % HP2, u = (it / HP2) % K::R1, b = it / (HP2 * K::R1);
-#pragma unroll
-                for (int q = 0; q < K::R2; ++q) {
-                    const Pair pr = ld_sh(buf + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp);
-                    ha[h][q] = pr.a;
-                    hb[h][q] = pr.b;
-                }
-                dft_small<K::R2, DIR>(ha[h]);
-                dft_small<K::R2, DIR>(hb[h]);
-            }
+        for (int q = 0; q < K::R2; ++q) {
+            const Pair pr = ld_sh(work + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp);
+            va[q] = pr.a;
+            vb[q] = pr.b;
         }
-        consumer_sync<K::NT>();
+        dft_small<K::R2, DIR>(va);
+        dft_small<K::R2, DIR>(vb);
+        const int s2 = 2 * sp;
 #pragma unroll
-        for (int h = 0; h < NB; ++h) {
-            const int it = tid + h * K::NT;
-            if (it < IB) {
-                const int sp = it % HP2, u = (it / HP2) % K::R1, b = it / (HP2 * K::R1);
-                const int s2 = 2 * sp;
-#pragma unroll
-                for (int vv = 0; vv < K::R2; ++vv) {
-                    const int k2 = u + K::R1 * vv;
-                    const float4 tt = T.tb[k2 * HP2 + sp];
-                    buf[x2_index<K>(b, k2, s2)] = cmul(ha[h][vv], make_float2(tt.x, tt.y));
-                    buf[x2_index<K>(b, k2, s2 + 1)] = cmul(hb[h][vv], make_float2(tt.z, tt.w));
-                }
-            }
+        for (int vv = 0; vv < K::R2; ++vv) {
+            const int k2 = u + K::R1 * vv;
+            const float4 tt = T.tb[k2 * HP2 + sp];
+            buf[x2_index<K>(b, k2, s2)] = cmul(va[vv], make_float2(tt.x, tt.y));
+            buf[x2_index<K>(b, k2, s2 + 1)] = cmul(vb[vv], make_float2(tt.z, tt.w));
         }
-        consumer_sync<K::NT>();
     }
-    // S1c: items (pair of adjacent i2' in Put order); F_B over b -> c; twiddle w_{L1}^{a c}; to scratch
+    consumer_sync<K::NT>();
+    // S1c (buf -> scratch): items (pair of adjacent i2' in Put order); F_B over b -> c; twiddle w_{L1}^{a c}
     constexpr int IC = K::N2 / 2;
     const int arow = m0 * K::A + (a ^ (m0 & K::SWA));
     unsigned long long pol = 0;
@@ -345,82 +301,52 @@ __device__ __forceinline__ void stage1_compute(const Geo &g, const Tabs &T, floa
 // buf: the L0 x A x W block of one (c, chunk), rows swizzled as stage 1 wrote them.
 // In place, shared layouts: Y1[e][m0][w]; Y2[e][u'][q''][w] with q'' = q' ^ (u' mod SW2).
 template <class K, int DIR>
-__device__ __forceinline__ void stage2_compute(const Geo &g, const Tabs &T, float2 *buf, int s0, int s1, int c,
-                                               int chunk) {
+__device__ __forceinline__ void stage2_compute(const Geo &g, const Tabs &T, float2 *buf, float2 *work, int s0, int s1,
+                                               int c, int chunk) {
     const int tid = threadIdx.x;
     constexpr int HW = K::W / 2;
-    // S2a: items (m0, w pair); F_A over a -> e; k1 = c + B e; twiddle w_{n1}^{k1 s1}
+    // S2a (buf -> work): items (m0, w pair); F_A over a -> e; k1 = c + B e; twiddle w_{n1}^{k1 s1}; Y1 layout
     constexpr int IA = K::L0 * HW;
-    constexpr int NA = (IA + K::NT - 1) / K::NT;
-    {
-        float2 ha[NA][K::A], hb[NA][K::A];
+    for (int it = tid; it < IA; it += K::NT) {
+        const int wp = it % HW, m0 = it / HW;
+        float2 va[K::A], vb[K::A];
 #pragma unroll
-        for (int h = 0; h < NA; ++h) {
-            const int it = tid + h * K::NT;
-            if (it < IA) {
-                const int wp = it % HW, m0 = it / HW;
-#pragma unroll
-                for (int a = 0; a < K::A; ++a) {
-                    const Pair pr = ld_sh(buf + (m0 * K::A + (a ^ (m0 & K::SWA))) * K::W + 2 * wp);
-                    ha[h][a] = pr.a;
-                    hb[h][a] = pr.b;
-                }
-                dft_small<K::A, DIR>(ha[h]);
-                dft_small<K::A, DIR>(hb[h]);
-            }
+        for (int a = 0; a < K::A; ++a) {
+            const Pair pr = ld_sh(buf + (m0 * K::A + (a ^ (m0 & K::SWA))) * K::W + 2 * wp);
+            va[a] = pr.a;
+            vb[a] = pr.b;
         }
-        consumer_sync<K::NT>();
+        dft_small<K::A, DIR>(va);
+        dft_small<K::A, DIR>(vb);
 #pragma unroll
-        for (int h = 0; h < NA; ++h) {
-            const int it = tid + h * K::NT;
-            if (it < IA) {
-                const int wp = it % HW, m0 = it / HW;
-#pragma unroll
-                for (int e = 0; e < K::A; ++e) {
-                    const float2 t = T.t1[((c + K::B * e) * s1) & (g.n1 - 1)];
-                    st_sh(buf + (e * K::L0 + m0) * K::W + 2 * wp, cmul(ha[h][e], t), cmul(hb[h][e], t));
-                }
-            }
+        for (int e = 0; e < K::A; ++e) {
+            const float2 t = T.t1[((c + K::B * e) * s1) & (g.n1 - 1)];
+            st_sh(work + (e * K::L0 + m0) * K::W + 2 * wp, cmul(va[e], t), cmul(vb[e], t));
         }
-        consumer_sync<K::NT>();
     }
-    // S2b: items (e, q', w pair); m0 = q' + Q2 r; F_{Q1} over r -> u'; twiddle w_{L0}^{q' u'}
+    consumer_sync<K::NT>();
+    // S2b (work -> buf): items (e, q', w pair); m0 = q' + Q2 r; F_{Q1} over r -> u'; twiddle w_{L0}^{q' u'}
     constexpr int IB = K::A * K::Q2 * HW;
-    constexpr int NB = (IB + K::NT - 1) / K::NT;
-    {
-        float2 ha[NB][K::Q1], hb[NB][K::Q1];
+    for (int it = tid; it < IB; it += K::NT) {
+        const int wp = it % HW, q = (it / HW) % K::Q2, e = it / (HW * K::Q2);
+        float2 va[K::Q1], vb[K::Q1];
 #pragma unroll
-        for (int h = 0; h < NB; ++h) {
-            const int it = tid + h * K::NT;
-            if (it < IB) {
-                const int wp = it % HW, q = (it / HW) % K::Q2, e = it / (HW * K::Q2);
-#pragma unroll
-                for (int r = 0; r < K::Q1; ++r) {
-                    const Pair pr = ld_sh(buf + (e * K::L0 + q + K::Q2 * r) * K::W + 2 * wp);
-                    ha[h][r] = pr.a;
-                    hb[h][r] = pr.b;
-                }
-                dft_small<K::Q1, DIR>(ha[h]);
-                dft_small<K::Q1, DIR>(hb[h]);
-            }
+        for (int r = 0; r < K::Q1; ++r) {
+            const Pair pr = ld_sh(work + (e * K::L0 + q + K::Q2 * r) * K::W + 2 * wp);
+            va[r] = pr.a;
+            vb[r] = pr.b;
         }
-        consumer_sync<K::NT>();
+        dft_small<K::Q1, DIR>(va);
+        dft_small<K::Q1, DIR>(vb);
 #pragma unroll
-        for (int h = 0; h < NB; ++h) {
-            const int it = tid + h * K::NT;
-            if (it < IB) {
-                const int wp = it % HW, q = (it / HW) % K::Q2, e = it / (HW * K::Q2);
-#pragma unroll
-                for (int u = 0; u < K::Q1; ++u) {
-                    const float2 t = T.td[u * K::Q2 + q];
-                    st_sh(buf + ((e * K::Q1 + u) * K::Q2 + (q ^ (u % K::SW2))) * K::W + 2 * wp, cmul(ha[h][u], t),
-                          cmul(hb[h][u], t));
-                }
-            }
+        for (int u = 0; u < K::Q1; ++u) {
+            const float2 t = T.td[u * K::Q2 + q];
+            st_sh(buf + ((e * K::Q1 + u) * K::Q2 + (q ^ (u % K::SW2))) * K::W + 2 * wp, cmul(va[u], t),
+                  cmul(vb[u], t));
         }
-        consumer_sync<K::NT>();
     }
-    // S2c: items (e, u', w pair); F_{Q2} over q' -> v'; k0 = u' + Q1 v'; twiddle w_{n0}^{k0 s0}; store
+    consumer_sync<K::NT>();
+    // S2c (buf -> HBM): items (e, u', w pair); F_{Q2} over q' -> v'; k0 = u' + Q1 v'; twiddle w_{n0}^{k0 s0}
     constexpr int IC = K::A * K::Q1 * HW;
     for (int it = tid; it < IC; it += K::NT) {
         const int wp = it % HW, u = (it / HW) % K::Q1, e = it / (HW * K::Q1);
@@ -484,7 +410,7 @@ __device__ __forceinline__ void decode_task(int t, int U, int mode, int &unit, i
 
 template <class K>
 __host__ __device__ constexpr size_t pipe_smem_bytes(int n0, int n1) {
-    return (size_t)K::NS * K::TILE * sizeof(float2) + table_elems<K>(n0, n1) * sizeof(float2) +
+    return (size_t)(K::NS + 1) * K::TILE * sizeof(float2) + table_elems<K>(n0, n1) * sizeof(float2) +
            2 * K::NS * sizeof(uint64_t) + K::NS * sizeof(int) + 16;
 }
 
@@ -492,7 +418,8 @@ template <class K, int DIR, int MODE>
 __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_constant__ Geo g) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2 *bufs = reinterpret_cast<float2 *>(smem_raw);
-    const Tabs T = build_tables<K, DIR>(g, smem_raw + (size_t)K::NS * K::TILE * sizeof(float2));
+    float2 *work = bufs + (size_t)K::NS * K::TILE;  // ping-pong partner of the landed buffer
+    const Tabs T = build_tables<K, DIR>(g, smem_raw + (size_t)(K::NS + 1) * K::TILE * sizeof(float2));
     uint64_t *full = reinterpret_cast<uint64_t *>(
         (reinterpret_cast<uintptr_t>(T.te + g.n0) + 7) & ~static_cast<uintptr_t>(7));
     uint64_t *empty = full + K::NS;
@@ -628,9 +555,9 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
         float2 *buf = bufs + (size_t)s * K::TILE;
         if (is_s1) {
             float2 *slot = g.scratch + (size_t)(MODE == 2 ? unit % g.ring : unit) * K::UNIT;
-            stage1_compute<K, DIR, MODE == 2>(g, T, buf, lt / K::A, lt % K::A, slot);
+            stage1_compute<K, DIR, MODE == 2>(g, T, buf, work, lt / K::A, lt % K::A, slot);
         } else {
-            stage2_compute<K, DIR>(g, T, buf, s0, s1, lt / K::NCH, lt % K::NCH);
+            stage2_compute<K, DIR>(g, T, buf, work, s0, s1, lt / K::NCH, lt % K::NCH);
             if (MODE == 2) {
                 // the block has been read: drop its L2 lines without write-back
                 const float2 *blk = g.scratch + (size_t)(unit % g.ring) * K::UNIT + (size_t)lt * K::TILE2;
