@@ -447,35 +447,51 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
         // output visible to the other CTAs.  Completed tasks are also published while the producer
         // waits on a dependency, so a CTA never waits on its own unpublished work.
         if (threadIdx.x != K::NT) return;
+        // pend[s]: task in buffer s not yet published (its consumers may still be running);
+        // unpub: released tasks waiting for the next publish (done after issuing the next copies,
+        // so the fence overlaps the transfer).  At most 2 NS entries are ever held.
         int pend_task[K::NS];
         unsigned pend_par[K::NS];
+        int unpub[2 * K::NS];
+        int n_unpub = 0;
         for (int s = 0; s < K::NS; ++s) {
             pend_task[s] = -1;
             pend_par[s] = 0;
         }
-        auto publish = [&](int s, bool block) -> bool {
+        auto release = [&](int s, bool block) -> bool {  // move a finished buffer's task to unpub
             if (pend_task[s] < 0) return true;
-            const bool done = block ? mbar_wait(empty + s, pend_par[s], g.spin_limit) : mbar_try(empty + s, pend_par[s]);
+            const bool done =
+                block ? mbar_wait(empty + s, pend_par[s], g.spin_limit) : mbar_try(empty + s, pend_par[s]);
             if (!done) return false;
-            if (MODE == 2) {
-                int unit, lt, is_s1;
-                decode_task<K>(pend_task[s], U, MODE, unit, lt, is_s1);
-                __threadfence();
-                atomicAdd(is_s1 ? s1_done + unit : s2_done + unit, 1u);
-            }
+            unpub[n_unpub++] = pend_task[s];
             pend_task[s] = -1;
             return true;
         };
+        auto publish = [&]() {
+            if (MODE != 2 || n_unpub == 0) {
+                n_unpub = 0;
+                return;
+            }
+            __threadfence();
+            for (int k = 0; k < n_unpub; ++k) {
+                int unit, lt, is_s1;
+                decode_task<K>(unpub[k], U, MODE, unit, lt, is_s1);
+                atomicAdd(is_s1 ? s1_done + unit : s2_done + unit, 1u);
+            }
+            n_unpub = 0;
+        };
         bool abort = false;
-        int i = 0;
-        for (;; ++i) {
+        int next_t = MODE == 2 ? (int)atomicAdd(task_ctr, 1u) : (int)blockIdx.x;
+        for (int i = 0;; ++i) {
             const int s = i % K::NS;
             const unsigned ph = (unsigned)(i / K::NS) & 1u;
-            if (i >= K::NS && !publish(s, true)) {  // buffer s free again
+            if (i >= K::NS && !release(s, true)) {  // buffer s free again
                 atomicCAS(g.status, 0, (int)FFTU_ERR_TIMEOUT);
                 abort = true;
             }
-            const int t = abort ? total : MODE == 2 ? (int)atomicAdd(task_ctr, 1u) : (int)blockIdx.x + i * (int)gridDim.x;
+            const int t = abort ? total : next_t;
+            if (t < total)  // prefetch the next task index; its latency overlaps this task's set-up
+                next_t = MODE == 2 ? (int)atomicAdd(task_ctr, 1u) : (int)blockIdx.x + (i + 1) * (int)gridDim.x;
             if (t >= total) {
                 task[s] = -1;
                 mbar_arrive(full + s);
@@ -499,7 +515,9 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
                         unsigned v;
                         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
                         if (v >= target) break;
-                        for (int o = 0; o < K::NS; ++o) publish(o, false);
+                        // never wait on our own finished but unpublished work
+                        for (int o = 0; o < K::NS; ++o) release(o, false);
+                        publish();
                         if ((long long)(global_ns() - t0) > g.spin_limit) {
                             atomicCAS(g.status, 0, (int)FFTU_ERR_TIMEOUT);
                             abort = true;
@@ -533,10 +551,12 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
                 mbar_arrive_tx(full + s, K::TILE2 * (unsigned)sizeof(float2));
                 bulk_g2s(dst, slot + (size_t)lt * K::TILE2, K::TILE2 * (unsigned)sizeof(float2), full + s);
             }
+            publish();
         }
         // publish the tasks still in flight (the consumers finish them before seeing the sentinel)
         for (int s = 0; s < K::NS; ++s)
-            if (!publish(s, true)) atomicCAS(g.status, 0, (int)FFTU_ERR_TIMEOUT);
+            if (!release(s, true)) atomicCAS(g.status, 0, (int)FFTU_ERR_TIMEOUT);
+        publish();
         return;
     }
     // ---------------- consumers ----------------
