@@ -84,6 +84,7 @@ struct Step {
 // scratch ring (kRingSlots units) is meant to stay resident in L2.
 constexpr int64_t kRingUnitMaxBytes = 16ll << 20;
 constexpr int kRingSlots = 3;
+constexpr int kRingLag = 1;  // stage 2 of unit u follows stage 1 of unit u + kRingLag (needs kRingLag < kRingSlots)
 constexpr long long kSpinLimitNs = 2000000000ll;
 
 }  // namespace
@@ -231,9 +232,10 @@ fftu_status build_fused_phase_a(Plan &pl, bool *used) {
     const int64_t unit_bytes = info.unit_elems * (int64_t)pl.esize;
     const int64_t units = pl.p[0] * pl.p[1];
     size_t ws;
-    if (unit_bytes <= kRingUnitMaxBytes && units > kRingSlots) {
+    if (unit_bytes <= kRingUnitMaxBytes && units > kRingSlots && units > kRingLag) {
         l.mode = 1;
         l.ring = kRingSlots;
+        l.lag = kRingLag;
         ws = (size_t)kRingSlots * unit_bytes + 256 + sizeof(unsigned) * (size_t)(1 + 2 * units);
     } else {
         l.mode = 0;

@@ -69,7 +69,7 @@ struct Phase3Launch {
     const void *tw[3];
     int *status;
     unsigned *counters;
-    int p0, p1, n0, n1, ring;
+    int p0, p1, n0, n1, ring, lag;
     int grid, grid1, grid2;  // persistent ring kernel; stage-1 and stage-2 kernels
     long long spin_limit_ns;
 };

@@ -164,6 +164,7 @@ extern "C" fftu_status fftu_exec_noalloc(int d, const int64_t *n, const int64_t 
         l.n0 = (int)n[0];
         l.n1 = (int)n[1];
         l.ring = kStaticRing;
+        l.lag = 1;
         l.grid1 = ds.grids[which][0];
         l.grid2 = ds.grids[which][1];
         l.grid = ds.grids[which][2];

@@ -75,6 +75,7 @@ struct Geo {
     int n0, n1;            // n_0 = P0 L0, n1 = P1 L1
     int units;             // P0 * P1
     int ring;              // ring slots (ring mode)
+    int lag;               // ring mode: stage 2 of unit u runs after stage 1 of unit u + lag (lag < ring)
     long long spin_limit;  // bounded-wait budget in nanoseconds
 };
 
@@ -378,33 +379,39 @@ __device__ __forceinline__ void stage2_compute(const Geo &g, const Tabs &T, floa
 // dependencies (ring), and lands each task's input in one of NS shared buffers with bulk copies
 // (B rows of N2 elements for stage 1, one contiguous block for stage 2), completing the buffer's
 // `full` mbarrier.  Consumers release a buffer through its `empty` mbarrier.
+// Ring order: group j = S1(j) (if j < U) followed by S2(j - lag) (if j >= lag), j = 0 .. U + lag - 1.
 template <class K>
-__device__ __forceinline__ void decode_task(int t, int U, int mode, int &unit, int &lt, int &is_s1) {
+__device__ __forceinline__ void decode_task(int t, int U, int mode, int lag, int &unit, int &lt, int &is_s1) {
+    constexpr int S1 = K::S1_TASKS, S2 = K::S2_TASKS;
     if (mode == 0) {
-        unit = t / K::S1_TASKS;
-        lt = t % K::S1_TASKS;
+        unit = t / S1;
+        lt = t % S1;
         is_s1 = 1;
     } else if (mode == 1) {
-        unit = t / K::S2_TASKS;
-        lt = t % K::S2_TASKS;
+        unit = t / S2;
+        lt = t % S2;
         is_s1 = 0;
-    } else if (t < K::S1_TASKS) {
-        unit = 0;
-        lt = t;
+    } else if (t < lag * S1) {  // groups 0 .. lag-1: stage 1 only
+        unit = t / S1;
+        lt = t % S1;
         is_s1 = 1;
-    } else {
-        const int r = t - K::S1_TASKS;
-        const int grp = K::S1_TASKS + K::S2_TASKS;
-        const int j = r / grp + 1, o = r % grp;
-        if (j < U && o < K::S1_TASKS) {
+    } else if (t < lag * S1 + (U - lag) * (S1 + S2)) {  // groups lag .. U-1: both
+        const int r = t - lag * S1;
+        const int j = r / (S1 + S2) + lag, o = r % (S1 + S2);
+        if (o < S1) {
             unit = j;
             lt = o;
             is_s1 = 1;
         } else {
-            unit = j - 1;
-            lt = j < U ? o - K::S1_TASKS : o;
+            unit = j - lag;
+            lt = o - S1;
             is_s1 = 0;
         }
+    } else {  // groups U .. U+lag-1: stage 2 only
+        const int r = t - lag * S1 - (U - lag) * (S1 + S2);
+        unit = U - lag + r / S2;
+        lt = r % S2;
+        is_s1 = 0;
     }
 }
 
@@ -475,13 +482,14 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
             __threadfence();
             for (int k = 0; k < n_unpub; ++k) {
                 int unit, lt, is_s1;
-                decode_task<K>(unpub[k], U, MODE, unit, lt, is_s1);
+                decode_task<K>(unpub[k], U, MODE, g.lag, unit, lt, is_s1);
                 atomicAdd(is_s1 ? s1_done + unit : s2_done + unit, 1u);
             }
             n_unpub = 0;
         };
         bool abort = false;
-        int next_t = MODE == 2 ? (int)atomicAdd(task_ctr, 1u) : (int)blockIdx.x;
+        constexpr bool kPrefetchTask = false;  // claim the next task one step early
+        int next_t = MODE == 2 ? (kPrefetchTask ? (int)atomicAdd(task_ctr, 1u) : -1) : (int)blockIdx.x;
         for (int i = 0;; ++i) {
             const int s = i % K::NS;
             const unsigned ph = (unsigned)(i / K::NS) & 1u;
@@ -489,16 +497,18 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
                 atomicCAS(g.status, 0, (int)FFTU_ERR_TIMEOUT);
                 abort = true;
             }
-            const int t = abort ? total : next_t;
-            if (t < total)  // prefetch the next task index; its latency overlaps this task's set-up
-                next_t = MODE == 2 ? (int)atomicAdd(task_ctr, 1u) : (int)blockIdx.x + (i + 1) * (int)gridDim.x;
+            int t = abort ? total : next_t;
+            if (MODE == 2 && !kPrefetchTask && !abort) t = (int)atomicAdd(task_ctr, 1u);
+            if (t < total)
+                next_t = MODE == 2 ? (kPrefetchTask ? (int)atomicAdd(task_ctr, 1u) : -1)
+                                   : (int)blockIdx.x + (i + 1) * (int)gridDim.x;
             if (t >= total) {
                 task[s] = -1;
                 mbar_arrive(full + s);
                 break;
             }
             int unit, lt, is_s1;
-            decode_task<K>(t, U, MODE, unit, lt, is_s1);
+            decode_task<K>(t, U, MODE, g.lag, unit, lt, is_s1);
             if (MODE == 2) {
                 const unsigned *ctr = nullptr;
                 unsigned target = 0;
@@ -570,7 +580,7 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
         const int t = task[s];
         if (t < 0) break;
         int unit, lt, is_s1;
-        decode_task<K>(t, U, MODE, unit, lt, is_s1);
+        decode_task<K>(t, U, MODE, g.lag, unit, lt, is_s1);
         const int s0 = unit / g.P1, s1 = unit % g.P1;
         float2 *buf = bufs + (size_t)s * K::TILE;
         if (is_s1) {
@@ -610,6 +620,7 @@ cudaError_t launch_k(const Phase3Launch &l, cudaStream_t st) {
     g.n1 = l.n1;
     g.units = l.p0 * l.p1;
     g.ring = l.ring;
+    g.lag = l.lag;
     g.spin_limit = l.spin_limit_ns;
     const size_t smem = pipe_smem_bytes<K>(l.n0, l.n1);
     if (l.mode == 0) {
