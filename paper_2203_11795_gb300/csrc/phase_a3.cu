@@ -455,8 +455,7 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
         // waits on a dependency, so a CTA never waits on its own unpublished work.
         if (threadIdx.x != K::NT) return;
         // pend[s]: task in buffer s not yet published (its consumers may still be running);
-        // unpub: released tasks waiting for the next publish (done after issuing the next copies,
-        // so the fence overlaps the transfer).  At most 2 NS entries are ever held.
+        // unpub: released tasks waiting to be published (at most 2 NS entries are ever held).
         int pend_task[K::NS];
         unsigned pend_par[K::NS];
         int unpub[2 * K::NS];
@@ -497,6 +496,7 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
                 atomicCAS(g.status, 0, (int)FFTU_ERR_TIMEOUT);
                 abort = true;
             }
+            publish();  // dependents in other CTAs are waiting for it: publish right away
             int t = abort ? total : next_t;
             if (MODE == 2 && !kPrefetchTask && !abort) t = (int)atomicAdd(task_ctr, 1u);
             if (t < total)
