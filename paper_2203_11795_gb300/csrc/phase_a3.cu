@@ -42,7 +42,7 @@ namespace fftu {
 
 namespace {
 
-template <int N2_, int P2_, int R1_, int B_, int A_, int L0_, int Q1_, int W_, int MINB_>
+template <int N2_, int P2_, int R1_, int B_, int A_, int L0_, int Q1_, int W_, int MINB_, int NS_, bool PP_>
 struct Cfg {
     static constexpr int N2 = N2_, P2 = P2_, L2 = N2 / P2, R1 = R1_, R2 = L2 / R1;
     static constexpr int B = B_, A = A_, L1 = A * B;
@@ -60,7 +60,8 @@ struct Cfg {
     static constexpr int SW1 = (16 / P2) < R2 ? (16 / P2) : R2;
     static constexpr int SW2 = (16 / W) < Q2 ? (16 / W) : Q2;
     static constexpr int SWA = ((16 / W) < A ? (16 / W) : A) - 1;  // scratch row swizzle mask
-    static constexpr int NS = 2;                 // shared input buffers (pipeline depth)
+    static constexpr int NS = NS_;               // shared input buffers (pipeline depth)
+    static constexpr bool PINGPONG = PP_;        // passes alternate with a work buffer (else in place)
 };
 
 // Run-time geometry shared by every task.
@@ -222,49 +223,91 @@ __device__ __forceinline__ void stage1_compute(const Geo &g, const Tabs &T, floa
                                                float2 *dst_unit) {
     const int tid = threadIdx.x;
     constexpr int HP2 = K::P2 / 2;
-    // S1a (buf -> work): items (b, s2 pair, q); inputs j = q + R2 r -> i2 = s2 + P2 q + (N2 / R1) r;
-    // F_{R1} over r -> u; twiddle w_{L2}^{q u}; X1 layout
+    // S1a (buf -> X1): items (b, s2 pair, q); inputs j = q + R2 r -> i2 = s2 + P2 q + (N2 / R1) r;
+    // F_{R1} over r -> u; twiddle w_{L2}^{q u}.  X1 goes to `work` (ping-pong) or back into `buf`.
+    float2 *x1 = K::PINGPONG ? work : buf;
     constexpr int IA = K::B * HP2 * K::R2;
-    for (int it = tid; it < IA; it += K::NT) {
-        const int sp = it % HP2, q = (it / HP2) % K::R2, b = it / (HP2 * K::R2);
-        float2 va[K::R1], vb[K::R1];
+    constexpr int NA = (IA + K::NT - 1) / K::NT;
+    {
+        float2 ha[NA][K::R1], hb[NA][K::R1];
 #pragma unroll
-        for (int r = 0; r < K::R1; ++r) {
-            const Pair pr = ld_sh(buf + b * K::N2 + 2 * sp + K::P2 * q + (K::N2 / K::R1) * r);
-            va[r] = pr.a;
-            vb[r] = pr.b;
+        for (int h = 0; h < NA; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IA) {
+                const int sp = it % HP2, q = (it / HP2) % K::R2, b = it / (HP2 * K::R2);
+#pragma unroll
+                for (int r = 0; r < K::R1; ++r) {
+                    const Pair pr = ld_sh(buf + b * K::N2 + 2 * sp + K::P2 * q + (K::N2 / K::R1) * r);
+                    ha[h][r] = pr.a;
+                    hb[h][r] = pr.b;
+                }
+                dft_small<K::R1, DIR>(ha[h]);
+                dft_small<K::R1, DIR>(hb[h]);
+            }
+            if (K::PINGPONG && it < IA) {
+                const int sp = it % HP2, q = (it / HP2) % K::R2, b = it / (HP2 * K::R2);
+#pragma unroll
+                for (int u = 0; u < K::R1; ++u) {
+                    const float2 w = T.ta[u * K::R2 + q];
+                    st_sh(x1 + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp, cmul(ha[h][u], w),
+                          cmul(hb[h][u], w));
+                }
+            }
         }
-        dft_small<K::R1, DIR>(va);
-        dft_small<K::R1, DIR>(vb);
+        if (!K::PINGPONG) {
+            consumer_sync<K::NT>();
 #pragma unroll
-        for (int u = 0; u < K::R1; ++u) {
-            const float2 w = T.ta[u * K::R2 + q];
-            st_sh(work + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp, cmul(va[u], w),
-                  cmul(vb[u], w));
+            for (int h = 0; h < NA; ++h) {
+                const int it = tid + h * K::NT;
+                if (it < IA) {
+                    const int sp = it % HP2, q = (it / HP2) % K::R2, b = it / (HP2 * K::R2);
+#pragma unroll
+                    for (int u = 0; u < K::R1; ++u) {
+                        const float2 w = T.ta[u * K::R2 + q];
+                        st_sh(x1 + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp,
+                              cmul(ha[h][u], w), cmul(hb[h][u], w));
+                    }
+                }
+            }
         }
     }
     consumer_sync<K::NT>();
-    // S1b (work -> buf): items (b, s2 pair, u); F_{R2} over q -> v; k2 = u + R1 v; twiddle w_{n2}^{k2 s2};
+    // S1b (X1 -> buf): items (b, s2 pair, u); F_{R2} over q -> v; k2 = u + R1 v; twiddle w_{n2}^{k2 s2};
     // Put order (X2 layout)
     constexpr int IB = K::B * HP2 * K::R1;
-    for (int it = tid; it < IB; it += K::NT) {
-        const int sp = it % HP2, u = (it / HP2) % K::R1, b = it / (HP2 * K::R1);
-        float2 va[K::R2], vb[K::R2];
+    constexpr int NB = (IB + K::NT - 1) / K::NT;
+    {
+        float2 ha[NB][K::R2], hb[NB][K::R2];
 #pragma unroll
-        for (int q = 0; q < K::R2; ++q) {
-            const Pair pr = ld_sh(work + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp);
-            va[q] = pr.a;
-            vb[q] = pr.b;
+        for (int h = 0; h < NB; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IB) {
+                const int sp = it % HP2, u = (it / HP2) % K::R1, b = it / (HP2 * K::R1);
+#pragma unroll
+                for (int q = 0; q < K::R2; ++q) {
+                    const Pair pr = ld_sh(x1 + ((b * K::R1 + u) * K::R2 + (q ^ (u % K::SW1))) * K::P2 + 2 * sp);
+                    ha[h][q] = pr.a;
+                    hb[h][q] = pr.b;
+                }
+                dft_small<K::R2, DIR>(ha[h]);
+                dft_small<K::R2, DIR>(hb[h]);
+            }
         }
-        dft_small<K::R2, DIR>(va);
-        dft_small<K::R2, DIR>(vb);
-        const int s2 = 2 * sp;
+        if (!K::PINGPONG) consumer_sync<K::NT>();
 #pragma unroll
-        for (int vv = 0; vv < K::R2; ++vv) {
-            const int k2 = u + K::R1 * vv;
-            const float4 tt = T.tb[k2 * HP2 + sp];
-            buf[x2_index<K>(b, k2, s2)] = cmul(va[vv], make_float2(tt.x, tt.y));
-            buf[x2_index<K>(b, k2, s2 + 1)] = cmul(vb[vv], make_float2(tt.z, tt.w));
+        for (int h = 0; h < NB; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IB) {
+                const int sp = it % HP2, u = (it / HP2) % K::R1, b = it / (HP2 * K::R1);
+                const int s2 = 2 * sp;
+#pragma unroll
+                for (int vv = 0; vv < K::R2; ++vv) {
+                    const int k2 = u + K::R1 * vv;
+                    const float4 tt = T.tb[k2 * HP2 + sp];
+                    buf[x2_index<K>(b, k2, s2)] = cmul(ha[h][vv], make_float2(tt.x, tt.y));
+                    buf[x2_index<K>(b, k2, s2 + 1)] = cmul(hb[h][vv], make_float2(tt.z, tt.w));
+                }
+            }
         }
     }
     consumer_sync<K::NT>();
@@ -306,44 +349,76 @@ __device__ __forceinline__ void stage2_compute(const Geo &g, const Tabs &T, floa
                                                int c, int chunk) {
     const int tid = threadIdx.x;
     constexpr int HW = K::W / 2;
-    // S2a (buf -> work): items (m0, w pair); F_A over a -> e; k1 = c + B e; twiddle w_{n1}^{k1 s1}; Y1 layout
+    // S2a (buf -> Y1): items (m0, w pair); F_A over a -> e; k1 = c + B e; twiddle w_{n1}^{k1 s1}.
+    // Y1 goes to `work` (ping-pong) or back into `buf`.
+    float2 *y1 = K::PINGPONG ? work : buf;
     constexpr int IA = K::L0 * HW;
-    for (int it = tid; it < IA; it += K::NT) {
-        const int wp = it % HW, m0 = it / HW;
-        float2 va[K::A], vb[K::A];
+    constexpr int NA = (IA + K::NT - 1) / K::NT;
+    {
+        float2 ha[NA][K::A], hb[NA][K::A];
 #pragma unroll
-        for (int a = 0; a < K::A; ++a) {
-            const Pair pr = ld_sh(buf + (m0 * K::A + (a ^ (m0 & K::SWA))) * K::W + 2 * wp);
-            va[a] = pr.a;
-            vb[a] = pr.b;
+        for (int h = 0; h < NA; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IA) {
+                const int wp = it % HW, m0 = it / HW;
+#pragma unroll
+                for (int a = 0; a < K::A; ++a) {
+                    const Pair pr = ld_sh(buf + (m0 * K::A + (a ^ (m0 & K::SWA))) * K::W + 2 * wp);
+                    ha[h][a] = pr.a;
+                    hb[h][a] = pr.b;
+                }
+                dft_small<K::A, DIR>(ha[h]);
+                dft_small<K::A, DIR>(hb[h]);
+            }
         }
-        dft_small<K::A, DIR>(va);
-        dft_small<K::A, DIR>(vb);
+        if (!K::PINGPONG) consumer_sync<K::NT>();
 #pragma unroll
-        for (int e = 0; e < K::A; ++e) {
-            const float2 t = T.t1[((c + K::B * e) * s1) & (g.n1 - 1)];
-            st_sh(work + (e * K::L0 + m0) * K::W + 2 * wp, cmul(va[e], t), cmul(vb[e], t));
+        for (int h = 0; h < NA; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IA) {
+                const int wp = it % HW, m0 = it / HW;
+#pragma unroll
+                for (int e = 0; e < K::A; ++e) {
+                    const float2 t = T.t1[((c + K::B * e) * s1) & (g.n1 - 1)];
+                    st_sh(y1 + (e * K::L0 + m0) * K::W + 2 * wp, cmul(ha[h][e], t), cmul(hb[h][e], t));
+                }
+            }
         }
     }
     consumer_sync<K::NT>();
-    // S2b (work -> buf): items (e, q', w pair); m0 = q' + Q2 r; F_{Q1} over r -> u'; twiddle w_{L0}^{q' u'}
+    // S2b (Y1 -> buf): items (e, q', w pair); m0 = q' + Q2 r; F_{Q1} over r -> u'; twiddle w_{L0}^{q' u'}
     constexpr int IB = K::A * K::Q2 * HW;
-    for (int it = tid; it < IB; it += K::NT) {
-        const int wp = it % HW, q = (it / HW) % K::Q2, e = it / (HW * K::Q2);
-        float2 va[K::Q1], vb[K::Q1];
+    constexpr int NB = (IB + K::NT - 1) / K::NT;
+    {
+        float2 ha[NB][K::Q1], hb[NB][K::Q1];
 #pragma unroll
-        for (int r = 0; r < K::Q1; ++r) {
-            const Pair pr = ld_sh(work + (e * K::L0 + q + K::Q2 * r) * K::W + 2 * wp);
-            va[r] = pr.a;
-            vb[r] = pr.b;
+        for (int h = 0; h < NB; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IB) {
+                const int wp = it % HW, q = (it / HW) % K::Q2, e = it / (HW * K::Q2);
+#pragma unroll
+                for (int r = 0; r < K::Q1; ++r) {
+                    const Pair pr = ld_sh(y1 + (e * K::L0 + q + K::Q2 * r) * K::W + 2 * wp);
+                    ha[h][r] = pr.a;
+                    hb[h][r] = pr.b;
+                }
+                dft_small<K::Q1, DIR>(ha[h]);
+                dft_small<K::Q1, DIR>(hb[h]);
+            }
         }
-        dft_small<K::Q1, DIR>(va);
-        dft_small<K::Q1, DIR>(vb);
+        if (!K::PINGPONG) consumer_sync<K::NT>();
 #pragma unroll
-        for (int u = 0; u < K::Q1; ++u) {
-            const float2 t = T.td[u * K::Q2 + q];
-            st_sh(buf + ((e * K::Q1 + u) * K::Q2 + (q ^ (u % K::SW2))) * K::W + 2 * wp, cmul(va[u], t),
-                  cmul(vb[u], t));
+        for (int h = 0; h < NB; ++h) {
+            const int it = tid + h * K::NT;
+            if (it < IB) {
+                const int wp = it % HW, q = (it / HW) % K::Q2, e = it / (HW * K::Q2);
+#pragma unroll
+                for (int u = 0; u < K::Q1; ++u) {
+                    const float2 t = T.td[u * K::Q2 + q];
+                    st_sh(buf + ((e * K::Q1 + u) * K::Q2 + (q ^ (u % K::SW2))) * K::W + 2 * wp, cmul(ha[h][u], t),
+                          cmul(hb[h][u], t));
+                }
+            }
         }
     }
     consumer_sync<K::NT>();
@@ -417,7 +492,7 @@ __device__ __forceinline__ void decode_task(int t, int U, int mode, int lag, int
 
 template <class K>
 __host__ __device__ constexpr size_t pipe_smem_bytes(int n0, int n1) {
-    return (size_t)(K::NS + 1) * K::TILE * sizeof(float2) + table_elems<K>(n0, n1) * sizeof(float2) +
+    return (size_t)(K::NS + (K::PINGPONG ? 1 : 0)) * K::TILE * sizeof(float2) + table_elems<K>(n0, n1) * sizeof(float2) +
            2 * K::NS * sizeof(uint64_t) + K::NS * sizeof(int) + 16;
 }
 
@@ -426,7 +501,8 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2 *bufs = reinterpret_cast<float2 *>(smem_raw);
     float2 *work = bufs + (size_t)K::NS * K::TILE;  // ping-pong partner of the landed buffer
-    const Tabs T = build_tables<K, DIR>(g, smem_raw + (size_t)(K::NS + 1) * K::TILE * sizeof(float2));
+    const Tabs T =
+        build_tables<K, DIR>(g, smem_raw + (size_t)(K::NS + (K::PINGPONG ? 1 : 0)) * K::TILE * sizeof(float2));
     uint64_t *full = reinterpret_cast<uint64_t *>(
         (reinterpret_cast<uintptr_t>(T.te + g.n0) + 7) & ~static_cast<uintptr_t>(7));
     uint64_t *empty = full + K::NS;
@@ -666,10 +742,12 @@ cudaError_t prepare_k(int n0, int n1, int *grids) {
 }
 
 // Instantiated configurations (complex64):
-//   512^3, p = 8^3: L = 64, rows 64 = 8 x 8, axis 1 = 8 x 8, axis 0 = 8 x 8, W = 8; 2 CTAs/SM
-//   512^3, p = 4^3: L = 128, rows 128 = 8 x 16, axis 1 = 16 x 8, axis 0 = 8 x 16, W = 4; 1 CTA/SM
-using K512p8 = Cfg<512, 8, 8, 8, 8, 64, 8, 8, 2>;
-using K512p4 = Cfg<512, 4, 8, 8, 16, 128, 8, 4, 1>;
+//   512^3, p = 8^3: L = 64, rows 64 = 8 x 8, axis 1 = 8 x 8, axis 0 = 8 x 8, W = 8;
+//                   three input buffers, passes in place, 2 CTAs/SM
+//   512^3, p = 4^3: L = 128, rows 128 = 8 x 16, axis 1 = 16 x 8, axis 0 = 8 x 16, W = 4;
+//                   two input buffers and a work buffer, 1 CTA/SM
+using K512p8 = Cfg<512, 8, 8, 8, 8, 64, 8, 8, 2, 3, false>;
+using K512p4 = Cfg<512, 4, 8, 8, 16, 128, 8, 4, 1, 2, true>;
 
 template <int DIR, bool PREP>
 cudaError_t dispatch(int which, const Phase3Launch *l, cudaStream_t st, int n0, int n1, int *grid, size_t *smem) {
