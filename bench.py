@@ -46,6 +46,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", default="512,512,512", help="oracle sample shape for cpu_baseline")
+    ap.add_argument("--cpu-reps", type=int, default=3, help="oracle forward+inverse repetitions for cpu_baseline")
     ap.add_argument("--ref-sample", default="256,256,256", help="oracle sample shape per reference step")
     a = ap.parse_args()
     a.warmup = max(3, a.warmup)
@@ -153,6 +154,22 @@ def traffic_for(kernel):
         return None
 
 
+def max_over_ranks(ms, device):
+    """Slowest rank's time (ms); plain value without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(bytes_per_rank, ms, world):
+    """Whole-job GB/s: the bytes of every replica over the slowest replica's time."""
+    return world * bytes_per_rank / (ms * 1e-3) / 1e9
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -251,10 +268,7 @@ def run_ours(args):
     total_ms = t_start.elapsed_time(t_end)
     phase_a = [ev[0].elapsed_time(ev[1]) for ev in events] + [ev[2].elapsed_time(ev[3]) for ev in events]
     phase_b = [ev[1].elapsed_time(ev[2]) for ev in events] + [ev[3].elapsed_time(ev[4]) for ev in events]
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = float(t_max.item())
+    total_ms = max_over_ranks(total_ms, dev)
 
     # parity of the timed output (round trip) so a fast wrong kernel cannot pass unnoticed
     rt_err = float((torch.linalg.vector_norm(z - x) / torch.linalg.vector_norm(x)).item())
@@ -275,18 +289,14 @@ def run_ours(args):
                 out_host.copy_(z, non_blocking=True)
             e1.record(stream)
         torch.cuda.synchronize(dev)
-        e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
-        e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(e2e_t.item())
-        e2e = {"value": world * 2 * alg_bytes(shape, esize) / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.e2e_steps, dev)
+        e2e = {"value": whole_job_value(2 * alg_bytes(shape, esize), e2e_ms, world), "unit": "GB/s",
                "h2d_bytes_per_step": N * esize, "d2h_bytes_per_step": N * esize, "ms_per_step": e2e_ms,
                "includes": "pinned H2D of the input, forward, inverse, D2H of the result"}
 
     if rank == 0:
         ms_per_step = total_ms / args.steps
-        value = world * 2 * alg_bytes(shape, esize) / (ms_per_step * 1e-3) / 1e9
+        value = whole_job_value(2 * alg_bytes(shape, esize), ms_per_step, world)
         peak, peak_kind = measured_peak()
         ta, tb = statistics.mean(phase_a), statistics.mean(phase_b)
         half = 2 * N * esize  # one HBM round trip: the algorithmic bytes of one phase
@@ -306,11 +316,12 @@ def run_ours(args):
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             sample = shape_of(args.cpu_sample)
-            t_cpu, cores = oracle_cpu_run(sample, args.seed)
+            t_cpu, cores = oracle_cpu_run(sample, args.seed, reps=args.cpu_reps)
             cpu = {"value": 2 * alg_bytes(sample, esize) / t_cpu / 1e9, "unit": "GB/s", "cores": cores,
-                   "kind": "oracle", "seconds": t_cpu,
-                   "sample": f"FP64 oracle forward+inverse of one {'x'.join(map(str, sample))} array "
-                             f"(same seeded inputs), GB/s scaled by 4*N*8 bytes per transform"}
+                   "kind": "oracle", "seconds_per_rep": t_cpu,
+                   "sample": f"FP64 oracle forward+inverse of one {'x'.join(map(str, sample))} array, "
+                             f"{args.cpu_reps} repetitions (same seeded inputs), GB/s scaled by 4*N*8 bytes "
+                             f"per transform"}
         line = {
             "metric": "3D FFT HBM GB/s (algorithmic bytes 4*N*8 per transform), forward+inverse",
             "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -32,7 +32,7 @@ template <typename C, int DIR, int R>
 __device__ __forceinline__ void stockham_stage(C *sm, const C *__restrict__ tw, const AxisPass &a, int Ns,
                                                int tid, int nthreads) {
     constexpr int B = ept<C>() / R > 0 ? ept<C>() / R : 1;  // butterflies per thread per stage
-    const int cols = a.G * a.V;
+    const int cols = a.Gt * a.V;
     const int per_col = a.len / R;
     const int total = cols * per_col;
     const int twstep = a.nl / (Ns * R);
@@ -44,8 +44,8 @@ __device__ __forceinline__ void stockham_stage(C *sm, const C *__restrict__ tw, 
             const int col = w % cols, b = w / cols;
             int base, js;
             if (a.contiguous) {
-                base = (col / a.G) * a.nl + (col % a.G);
-                js = a.G;
+                base = (col / a.Gt) * a.nlt + (col % a.Gt);
+                js = a.Gt;
             } else {
                 base = col;
                 js = cols;
@@ -68,8 +68,8 @@ __device__ __forceinline__ void stockham_stage(C *sm, const C *__restrict__ tw, 
             const int col = w % cols, b = w / cols;
             int base, js;
             if (a.contiguous) {
-                base = (col / a.G) * a.nl + (col % a.G);
-                js = a.G;
+                base = (col / a.Gt) * a.nlt + (col % a.Gt);
+                js = a.Gt;
             } else {
                 base = col;
                 js = cols;
@@ -94,17 +94,31 @@ __global__ void __launch_bounds__(kAxisThreads) axis_pass_kernel(const __grid_co
     using Rl = typename real_of<C>::type;
     const int tid = threadIdx.x, nt = blockDim.x;
 
+    const int chunks = a.G / a.Gt;  // class chunks per line
     for (int64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) {
-        int64_t gbase;
+        const int cc = (int)(t % chunks);
+        const int64_t tt = t / chunks;
+        const int c0 = cc * a.Gt;
+        int64_t gbase;  // element offset of (first line or vector, line position 0)
         if (a.contiguous) {
-            gbase = t * (int64_t)a.V * a.nl;
+            gbase = tt * (int64_t)a.V * a.nl;
         } else {
             const int64_t tpo = a.inner / a.V;
-            gbase = (t / tpo) * (int64_t)a.nl * a.inner + (t % tpo) * a.V;
+            gbase = (tt / tpo) * (int64_t)a.nl * a.inner + (tt % tpo) * a.V;
         }
-        // load: shared index e is the natural order of the tile
+        // load: shared index e is the natural order of the tile (tile line position lp, vector v);
+        // tile position lp = c_local + j Gt holds line position c0 + c_local + j G
         for (int e = tid; e < a.tile; e += nt) {
-            int64_t g = a.contiguous ? gbase + e : gbase + (int64_t)(e / a.V) * a.inner + (e % a.V);
+            int lp, v;
+            if (a.contiguous) {
+                v = e / a.nlt;
+                lp = e % a.nlt;
+            } else {
+                lp = e / a.V;
+                v = e % a.V;
+            }
+            const int64_t gp = c0 + lp % a.Gt + (int64_t)(lp / a.Gt) * a.G;
+            const int64_t g = a.contiguous ? gbase + (int64_t)v * a.nl + gp : gbase + gp * a.inner + v;
             sm[e] = src[g];
         }
         __syncthreads();
@@ -119,25 +133,29 @@ __global__ void __launch_bounds__(kAxisThreads) axis_pass_kernel(const __grid_co
         // store with the output permutation, twiddle and scale
         const Rl scale = (Rl)a.scale;
         for (int e = tid; e < a.tile; e += nt) {
-            int lp, vv;  // output line position and vector
+            int lpo, v;  // tile output position and vector
             if (a.contiguous) {
-                vv = e / a.nl;
-                lp = e % a.nl;
+                v = e / a.nlt;
+                lpo = e % a.nlt;
             } else {
-                lp = e / a.V;
-                vv = e % a.V;
+                lpo = e / a.V;
+                v = e % a.V;
             }
             C val;
+            int64_t gp;  // global line position of the output
             if (a.mode == 0) {
-                const int c = lp / a.len, m = lp % a.len;
-                const int src_lp = c + m * a.G;
-                val = sm[a.contiguous ? vv * a.nl + src_lp : src_lp * a.V + vv];
+                const int cl = lpo / a.len, m = lpo % a.len;
+                const int c = c0 + cl;
+                const int src_lp = cl + m * a.Gt;
+                val = sm[a.contiguous ? v * a.nlt + src_lp : src_lp * a.V + v];
                 if (c != 0 && m != 0) val = cmul(val, dirw<DIR>(tw[c * m]));
+                gp = (int64_t)c * a.len + m;
             } else {
                 val = sm[e];
+                gp = c0 + lpo % a.Gt + (int64_t)(lpo / a.Gt) * a.G;
             }
             if (a.scale != 1.0) val = cscale(val, scale);
-            int64_t g = a.contiguous ? gbase + e : gbase + (int64_t)lp * a.inner + vv;
+            const int64_t g = a.contiguous ? gbase + (int64_t)v * a.nl + gp : gbase + gp * a.inner + v;
             dst[g] = val;
         }
         __syncthreads();

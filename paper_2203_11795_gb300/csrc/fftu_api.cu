@@ -104,6 +104,7 @@ struct Plan {
     int *dstatus = nullptr;
     std::vector<Step> phase_a, phase_b;
     std::vector<Step> phase_a_inplace;  // used when in == out and phase_a cannot run in place
+    bool generic_pingpong = false;      // generic phase A alternates between out and the workspace
 
     const void *table(int l) const { return static_cast<const char *>(tables) + table_off[l] * esize; }
 };
@@ -120,11 +121,6 @@ fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPa
     const int64_t nl = pl.n[l], Ll = pl.n[l] / pl.p[l];
     const int64_t target = is_double ? 4096 : 8192;
     const int64_t maxtile = is_double ? kMaxGenericTile / 4 : kMaxGenericTile / 2;
-    if (nl > maxtile) {
-        set_err("axis %d: length %lld exceeds the generic pass tile limit %lld", l, (long long)nl,
-                (long long)maxtile);
-        return FFTU_ERR_UNSUPPORTED;
-    }
     a.outer = outer;
     a.inner = inner;
     a.nl = (int)nl;
@@ -135,15 +131,31 @@ fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPa
         a.len = (int)pl.p[l];
         a.G = (int)Ll;
     }
+    if (a.len > maxtile) {
+        set_err("axis %d: sub-FFT length %d exceeds the generic pass tile limit %lld", l, a.len, (long long)maxtile);
+        return FFTU_ERR_UNSUPPORTED;
+    }
     a.mode = mode;
     a.contiguous = inner == 1;
-    int64_t V = target / nl;
-    if (V < 1) V = 1;
-    const int64_t cap = a.contiguous ? outer : inner;
-    if (V > cap) V = cap;
+    int64_t V, Gt;
+    if (nl <= maxtile) {  // whole lines: the pass can run in place
+        V = target / nl;
+        if (V < 1) V = 1;
+        const int64_t cap = a.contiguous ? outer : inner;
+        if (V > cap) V = cap;
+        Gt = a.G;
+    } else {  // long line: a tile takes Gt of the G classes (runs of Gt along the line, or V across it)
+        V = a.contiguous ? 1 : (inner < (is_double ? 4 : 8) ? inner : (is_double ? 4 : 8));
+        Gt = maxtile / (a.len * V);
+        if (Gt < 1) Gt = 1;
+        if (Gt > a.G) Gt = a.G;
+    }
     a.V = (int)V;
-    a.tile = (int)(nl * V);
-    a.tiles = a.contiguous ? outer / V : outer * (inner / V);
+    a.Gt = (int)Gt;
+    a.nlt = (int)(Gt * a.len);
+    a.tile = (int)(a.nlt * V);
+    const int64_t chunks = a.G / a.Gt;
+    a.tiles = (a.contiguous ? outer / V : outer * (inner / V)) * chunks;
     const int ept = is_double ? kEptMax / 2 : kEptMax;
     int th = (a.tile + ept - 1) / ept;
     th = ((th + 31) / 32) * 32;
@@ -268,6 +280,21 @@ fftu_status build_schedule(Plan &pl, int sched) {
     {
         fftu_status st = build_generic_phase_a(pl, fused_a ? pl.phase_a_inplace : pl.phase_a);
         if (st != FFTU_OK) return st;
+    }
+    if (!fused_a) {
+        // a pass over part of the classes of a line is not in place: alternate with a workspace
+        for (const Step &s : pl.phase_a)
+            if (s.kind == STEP_AXIS && s.axis.Gt < s.axis.G) pl.generic_pingpong = true;
+        if (pl.generic_pingpong) {
+            const size_t ws = (size_t)pl.N * pl.esize;
+            cudaError_t e = cudaMalloc(&pl.workspace, ws);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                set_err("cudaMalloc of %zu workspace bytes: %s", ws, cudaGetErrorString(e));
+                return FFTU_ERR_NOMEM;
+            }
+            pl.workspace_bytes = ws;
+        }
     }
     // Phase B: one fused pass when every p_l <= 16, else one pass per axis.
     Step s;
@@ -541,6 +568,25 @@ fftu_status fftu_exec_phase(fftu_handle h, fftu_phase phase, const void *in, voi
         return FFTU_ERR_ARG;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((phase & FFTU_PHASE_A) && pl->generic_pingpong) {
+        // buffers: pass k (of d) writes out when d - k is even, the workspace otherwise
+        const int np = (int)pl->phase_a.size();
+        const void *src = in;
+        for (int k = 1; k <= np; ++k) {
+            void *dst = ((np - k) % 2 == 0) ? out : pl->workspace;
+            if (dst == src) {
+                set_err("in-place transform with a long-line axis needs in != out");
+                return FFTU_ERR_UNSUPPORTED;
+            }
+            AxisPass a = pl->phase_a[k - 1].axis;
+            a.src = src;
+            a.dst = dst;
+            cudaError_t e = launch_axis_pass(a, pl->dtype == FFTU_C128, pl->dir, st);
+            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+            src = dst;
+        }
+        phase = (fftu_phase)(phase & ~FFTU_PHASE_A);
+    }
     if (phase & FFTU_PHASE_A) {
         // the persistent phase-A kernel reads `in` while writing `out`; in place it
         // would overwrite inputs other units have not read yet

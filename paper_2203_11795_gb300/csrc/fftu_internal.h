@@ -31,7 +31,9 @@ struct AxisPass {
     int mode;
     int V;            // vectors per tile: inner indices (strided axis) or lines (contiguous axis)
     int contiguous;   // inner == 1
-    int tile;         // nl * V
+    int Gt;           // classes per tile (G for whole lines; fewer for long lines)
+    int nlt;          // Gt * len: tile line length
+    int tile;         // nlt * V
     int threads;
     const void *tw;   // w_{nl}^e, e in [nl] (forward roots)
     double scale;

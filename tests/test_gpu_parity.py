@@ -175,3 +175,56 @@ def test_full_size_512_forward_inverse(fftu, shape, p):
     assert oracle.rel_l2(y.cpu().numpy(), ref) <= tolerance(np.complex64, N)
     del ref
     assert oracle.rel_l2(back.cpu().numpy(), x) <= tolerance(np.complex64, N)
+
+
+# ---- long lines (a tile holds part of the residue classes of a line) ------------------------
+
+@pytest.mark.parametrize("case", [((32768,), (128,), np.complex64),
+                                  ((16384, 16), (128, 4), np.complex64),
+                                  ((8, 8192), (2, 64), np.complex128)], ids=_id)
+@pytest.mark.parametrize("inverse", [False, True])
+def test_long_lines(fftu, case, inverse):
+    shape, p, dt = case
+    x = complex_uniform(515, shape, dtype=dt)
+    y, info = run_gpu(fftu, x, p, inverse=inverse)
+    assert info["workspace_bytes"] == x.size * x.itemsize  # phase A alternates with a workspace
+    assert oracle.rel_l2(y, oracle.fftn(x.astype(np.complex128), inverse=inverse)) <= tolerance(dt, x.size)
+
+
+def test_full_size_2d_16384(fftu):
+    """The 2D 16384 x 16384 complex64 workload (p = 128 x 128) against the full FP64 oracle."""
+    shape, p = (16384, 16384), (128, 128)
+    x = complex_uniform(2025, shape, dtype=np.complex64)
+    y, _ = run_gpu(fftu, x, p)
+    ref = oracle.fftn(x.astype(np.complex128))
+    assert oracle.rel_l2(y, ref) <= tolerance(np.complex64, x.size)
+
+
+@pytest.mark.parametrize("p", [(8, 8, 8), (4, 4, 4)], ids=["p8", "p4"])
+def test_full_size_1024_sampled(fftu, p):
+    """1024^3 complex64: forward at sampled outputs (direct O(N) sums of eq. dftd), round trip
+    and Parseval over the whole array."""
+    import torch
+    shape = (1024, 1024, 1024)
+    x = complex_uniform(2026, shape, dtype=np.complex64)
+    xt = torch.from_numpy(x).cuda()
+    with fftu.Plan(shape, p) as fwd, fftu.Plan(shape, p, inverse=True) as inv:
+        y = fwd.exec(xt)
+        back = inv.exec(y)
+        torch.cuda.synchronize()
+        fwd.check_device_status()
+    N = x.size
+    tol = tolerance(np.complex64, N)
+    rt = float((torch.linalg.vector_norm(back - xt) / torch.linalg.vector_norm(xt)).item())
+    assert rt <= tol
+    ex = torch.sum(torch.abs(xt.to(torch.complex128)) ** 2).item()
+    ey = torch.sum(torch.abs(y.to(torch.complex128)) ** 2).item()
+    assert abs(ey / (N * ex) - 1.0) <= tol
+    rng = np.random.default_rng(7)
+    ks = np.stack([rng.integers(0, 1024, 12) for _ in range(3)], axis=1)
+    ks[0] = (0, 0, 0)
+    ks[1] = (1023, 511, 1)
+    got = y.cpu().numpy()[tuple(ks.T)]
+    ref = oracle.dft_points(x, ks)
+    # relative to the typical output magnitude sqrt(N) (Parseval), per point
+    assert np.max(np.abs(got - ref)) / math.sqrt(N * 2.0 / 3.0) <= tol
