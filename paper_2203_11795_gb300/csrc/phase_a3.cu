@@ -42,7 +42,8 @@ namespace fftu {
 
 namespace {
 
-template <int N2_, int P2_, int R1_, int B_, int A_, int L0_, int Q1_, int W_, int MINB_, int NS_, bool PP_>
+template <int N2_, int P2_, int R1_, int B_, int A_, int L0_, int Q1_, int W_, int MINB_, int NS_, bool PP_,
+          bool GT_ = false>
 struct Cfg {
     static constexpr int N2 = N2_, P2 = P2_, L2 = N2 / P2, R1 = R1_, R2 = L2 / R1;
     static constexpr int B = B_, A = A_, L1 = A * B;
@@ -62,6 +63,7 @@ struct Cfg {
     static constexpr int SWA = ((16 / W) < A ? (16 / W) : A) - 1;  // scratch row swizzle mask
     static constexpr int NS = NS_;               // shared input buffers (pipeline depth)
     static constexpr bool PINGPONG = PP_;        // passes alternate with a work buffer (else in place)
+    static constexpr bool GLOBAL_T = GT_;        // the broadcast twiddles (t1, te) stay in global memory
 };
 
 // Run-time geometry shared by every task.
@@ -102,7 +104,7 @@ struct Tabs {
 
 template <class K>
 __host__ __device__ constexpr size_t table_elems(int n0, int n1) {
-    return (size_t)K::L2 * K::P2 + K::R1 * K::R2 + K::Q1 * K::Q2 + n1 + n0;
+    return (size_t)K::L2 * K::P2 + K::R1 * K::R2 + K::Q1 * K::Q2 + (K::GLOBAL_T ? 0 : n1 + n0);
 }
 
 template <class K, int DIR>
@@ -113,7 +115,7 @@ __device__ __forceinline__ Tabs build_tables(const Geo &g, unsigned char *raw) {
     T.ta = reinterpret_cast<float2 *>(T.tb + K::L2 * K::P2 / 2);
     T.td = T.ta + K::R1 * K::R2;
     T.t1 = T.td + K::Q1 * K::Q2;
-    T.te = T.t1 + g.n1;
+    T.te = T.t1 + (K::GLOBAL_T ? 0 : g.n1);
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int i = tid; i < K::L2 * K::P2 / 2; i += nt) {
         const int k2 = i / (K::P2 / 2), s2 = 2 * (i % (K::P2 / 2));
@@ -124,13 +126,27 @@ __device__ __forceinline__ Tabs build_tables(const Geo &g, unsigned char *raw) {
         T.ta[i] = tw_at<DIR>(g.tw2, ((i % K::R2) * (i / K::R2) * K::P2) & (K::N2 - 1));
     for (int i = tid; i < K::Q1 * K::Q2; i += nt)
         T.td[i] = tw_at<DIR>(g.tw0, ((i % K::Q2) * (i / K::Q2) * g.P0) & (g.n0 - 1));
-    for (int i = tid; i < g.n1; i += nt) T.t1[i] = tw_at<DIR>(g.tw1, i);
-    for (int i = tid; i < g.n0; i += nt) {
+    if (!K::GLOBAL_T)
+        for (int i = tid; i < g.n1; i += nt) T.t1[i] = tw_at<DIR>(g.tw1, i);
+    for (int i = tid; i < (K::GLOBAL_T ? 0 : g.n0); i += nt) {
         const int s0 = i / K::L0, k0 = i % K::L0;
         T.te[i] = tw_at<DIR>(g.tw0, (k0 * s0) & (g.n0 - 1));
     }
     __syncthreads();
     return T;
+}
+
+// The broadcast-style twiddles: w_{n1}^e (all lanes read one entry) and w_{n0}^{k0 s0} (lanes read
+// consecutive k0), from shared memory or, with GLOBAL_T, through the read-only L1 path.
+template <class K, int DIR>
+__device__ __forceinline__ float2 t1_at(const Geo &g, const Tabs &T, int e) {
+    if constexpr (K::GLOBAL_T) return dirw<DIR>(__ldg(g.tw1 + e));
+    return T.t1[e];
+}
+template <class K, int DIR>
+__device__ __forceinline__ float2 te_at(const Geo &g, const Tabs &T, int s0, int k0) {
+    if constexpr (K::GLOBAL_T) return dirw<DIR>(__ldg(g.tw0 + ((k0 * s0) & (g.n0 - 1))));
+    return T.te[s0 * K::L0 + k0];
 }
 
 // Scratch stores of the ring keep their lines in L2 (evict-last policy); the
@@ -331,7 +347,7 @@ __device__ __forceinline__ void stage1_compute(const Geo &g, const Tabs &T, floa
         float2 *d = dst_unit + (size_t)(ip / K::W) * K::TILE2 + arow * K::W + ip % K::W;
 #pragma unroll
         for (int c = 0; c < K::B; ++c) {
-            const float2 t = T.t1[(a * c * g.P1) & (g.n1 - 1)];
+            const float2 t = t1_at<K, DIR>(g, T, (a * c * g.P1) & (g.n1 - 1));
             float2 *dc = d + (size_t)c * K::NCH * K::TILE2;
             if constexpr (RING)
                 st_keep(dc, cmul(va[c], t), cmul(vb[c], t), pol);
@@ -379,7 +395,7 @@ __device__ __forceinline__ void stage2_compute(const Geo &g, const Tabs &T, floa
                 const int wp = it % HW, m0 = it / HW;
 #pragma unroll
                 for (int e = 0; e < K::A; ++e) {
-                    const float2 t = T.t1[((c + K::B * e) * s1) & (g.n1 - 1)];
+                    const float2 t = t1_at<K, DIR>(g, T, ((c + K::B * e) * s1) & (g.n1 - 1));
                     st_sh(y1 + (e * K::L0 + m0) * K::W + 2 * wp, cmul(ha[h][e], t), cmul(hb[h][e], t));
                 }
             }
@@ -439,7 +455,7 @@ __device__ __forceinline__ void stage2_compute(const Geo &g, const Tabs &T, floa
 #pragma unroll
         for (int vv = 0; vv < K::Q2; ++vv) {
             const int k0 = u + K::Q1 * vv;
-            const float2 t = T.te[s0 * K::L0 + k0];
+            const float2 t = te_at<K, DIR>(g, T, s0, k0);
             st_stream(dst + (size_t)(k0 + K::L0 * s0) * g.n1 * K::N2, cmul(va[vv], t), cmul(vb[vv], t));
         }
     }
@@ -504,7 +520,7 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
     const Tabs T =
         build_tables<K, DIR>(g, smem_raw + (size_t)(K::NS + (K::PINGPONG ? 1 : 0)) * K::TILE * sizeof(float2));
     uint64_t *full = reinterpret_cast<uint64_t *>(
-        (reinterpret_cast<uintptr_t>(T.te + g.n0) + 7) & ~static_cast<uintptr_t>(7));
+        (reinterpret_cast<uintptr_t>(T.te + (K::GLOBAL_T ? 0 : g.n0)) + 7) & ~static_cast<uintptr_t>(7));
     uint64_t *empty = full + K::NS;
     int *task = reinterpret_cast<int *>(empty + K::NS);
     if (threadIdx.x == 0) {
@@ -746,7 +762,7 @@ cudaError_t prepare_k(int n0, int n1, int *grids) {
 //                   three input buffers, passes in place, 2 CTAs/SM
 //   512^3, p = 4^3: L = 128, rows 128 = 8 x 16, axis 1 = 16 x 8, axis 0 = 8 x 16, W = 4;
 //                   two input buffers and a work buffer, 1 CTA/SM
-using K512p8 = Cfg<512, 8, 8, 8, 8, 64, 8, 8, 2, 3, false>;
+using K512p8 = Cfg<512, 8, 8, 8, 8, 64, 8, 8, 3, 2, false, true>;
 using K512p4 = Cfg<512, 4, 8, 8, 16, 128, 8, 4, 1, 2, true>;
 
 template <int DIR, bool PREP>
