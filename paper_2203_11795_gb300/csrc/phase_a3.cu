@@ -759,10 +759,11 @@ cudaError_t prepare_k(int n0, int n1, int *grids) {
 
 // Instantiated configurations (complex64):
 //   512^3, p = 8^3: L = 64, rows 64 = 8 x 8, axis 1 = 8 x 8, axis 0 = 8 x 8, W = 8;
-//                   three input buffers, passes in place, 2 CTAs/SM
+//                   two input buffers and a work buffer, 2 CTAs/SM (measured fastest among
+//                   {2, 3} buffers x {in place, ping-pong} x {2, 3} CTAs/SM)
 //   512^3, p = 4^3: L = 128, rows 128 = 8 x 16, axis 1 = 16 x 8, axis 0 = 8 x 16, W = 4;
 //                   two input buffers and a work buffer, 1 CTA/SM
-using K512p8 = Cfg<512, 8, 8, 8, 8, 64, 8, 8, 3, 2, false, true>;
+using K512p8 = Cfg<512, 8, 8, 8, 8, 64, 8, 8, 2, 2, true, false>;
 using K512p4 = Cfg<512, 4, 8, 8, 16, 128, 8, 4, 1, 2, true>;
 
 template <int DIR, bool PREP>
