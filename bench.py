@@ -30,6 +30,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
+METRIC = "3D FFT HBM GB/s & % roofline at 512^3 c64; mixed-request p50/p99 latency"
+METRIC_DETAIL = ("algorithmic HBM GB/s, B_alg = 4 N b bytes per transform (b = element size), "
+                 "one forward + one inverse transform per step; the serving latency part is not built")
 
 
 def parse_args():
@@ -41,6 +44,7 @@ def parse_args():
     ap.add_argument("--shape", default="512,512,512")
     ap.add_argument("--p", default="8,8,8")
     ap.add_argument("--schedule", type=int, default=0, help="0 auto, 1 generic, 2 fused")
+    ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -184,7 +188,7 @@ def run_reference(args):
     t = sum(times) / len(times)
     value = 2 * alg_bytes(sample, 8) / t / 1e9
     line = {
-        "metric": "3D FFT HBM GB/s (algorithmic bytes 4*N*8 per transform), forward+inverse",
+        "metric": METRIC, "metric_detail": METRIC_DETAIL,
         "value": value, "unit": "GB/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -216,13 +220,14 @@ def run_ours(args):
 
     shape, p = shape_of(args.shape), shape_of(args.p)
     N = math.prod(shape)
-    esize = 8
-    x_host = torch.from_numpy(complex_uniform(args.seed + rank, shape, dtype=np.complex64)).pin_memory()
+    np_dtype, t_dtype = (np.complex64, torch.complex64) if args.dtype == "c64" else (np.complex128, torch.complex128)
+    esize = 8 if args.dtype == "c64" else 16
+    x_host = torch.from_numpy(complex_uniform(args.seed + rank, shape, dtype=np_dtype)).pin_memory()
     x = x_host.to(dev)
     y = torch.empty_like(x)
     z = torch.empty_like(x)
-    fwd = fftu.Plan(shape, p, dtype=torch.complex64, schedule=args.schedule)
-    inv = fftu.Plan(shape, p, dtype=torch.complex64, inverse=True, schedule=args.schedule)
+    fwd = fftu.Plan(shape, p, dtype=t_dtype, schedule=args.schedule)
+    inv = fftu.Plan(shape, p, dtype=t_dtype, inverse=True, schedule=args.schedule)
     stream = torch.cuda.Stream(dev)
     sh = stream.cuda_stream
     A, B = fftu.FFTU_PHASE_A, fftu.FFTU_PHASE_B
@@ -323,14 +328,16 @@ def run_ours(args):
                              f"{args.cpu_reps} repetitions (same seeded inputs), GB/s scaled by 4*N*8 bytes "
                              f"per transform"}
         line = {
-            "metric": "3D FFT HBM GB/s (algorithmic bytes 4*N*8 per transform), forward+inverse",
+            "metric": METRIC, "metric_detail": METRIC_DETAIL,
             "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{'x'.join(map(str, shape))} complex64 forward+inverse FFT, cyclic "
+            "dtype": "f32" if esize == 8 else "f64", "data": "synthetic",
+            "config": {"workload": f"{'x'.join(map(str, shape))} complex{'64' if esize == 8 else '128'} "
+                                   f"forward+inverse FFT, cyclic "
                                    f"p={'x'.join(map(str, p))}",
                        "shape": list(shape), "p": list(p), "schedule": fwd.info["schedule"],
-                       "l2": "inputs (N*8 bytes) larger than L2 (129 MB); no flush",
+                       "l2": ("inputs larger than L2 (129 MB); no flush" if N * esize > 129e6 else
+                              "inputs smaller than L2: L2-resident, not an HBM measurement"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "gflops_5NlogN": world * 2 * 5 * N * math.log2(N) / (ms_per_step * 1e-3) / 1e9},
             "roofline": roofline,
