@@ -156,6 +156,13 @@ fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPa
     a.tile = (int)(a.nlt * V);
     const int64_t chunks = a.G / a.Gt;
     a.tiles = (a.contiguous ? outer / V : outer * (inner / V)) * chunks;
+    a.lg_V = ilog2(a.V);
+    a.lg_Gt = ilog2(a.Gt);
+    a.lg_nlt = ilog2(a.nlt);
+    a.lg_len = ilog2(a.len);
+    a.lg_G = ilog2(a.G);
+    a.lg_chunks = ilog2(chunks);
+    a.lg_tpo = a.contiguous ? 0 : ilog2(inner / V);
     const int ept = is_double ? kEptMax / 2 : kEptMax;
     int th = (a.tile + ept - 1) / ept;
     th = ((th + 31) / 32) * 32;
@@ -187,11 +194,16 @@ bool make_phase_b_fused(const Plan &pl, double scale, PhaseBFused &b) {
         stride *= pl.n[l];
     }
     b.P = P;
+    for (int l = 0; l < pl.d; ++l) {
+        b.lg_p[l] = ilog2(b.p[l]);
+        b.lg_L[l] = ilog2(b.L[l]);
+    }
     const size_t budget = 64 * 1024;
     int64_t Mt = b.L[pl.d - 1];
     while (Mt > 1 && (size_t)P * Mt * es > budget) Mt /= 2;
     if ((size_t)P * Mt * es > (size_t)kMaxDynSmem) return false;
     b.Mt = (int)Mt;
+    b.lg_Mt = ilog2(Mt);
     int64_t groups = 1;
     for (int l = 0; l < pl.d - 1; ++l) groups *= b.L[l];
     b.tiles = groups * (b.L[pl.d - 1] / Mt);

@@ -33,6 +33,8 @@ struct AxisPass {
     int contiguous;   // inner == 1
     int Gt;           // classes per tile (G for whole lines; fewer for long lines)
     int nlt;          // Gt * len: tile line length
+    // log2 of the power-of-two sizes above (index arithmetic uses shifts and masks)
+    int lg_V, lg_Gt, lg_nlt, lg_len, lg_G, lg_chunks, lg_tpo;
     int tile;         // nlt * V
     int threads;
     const void *tw;   // w_{nl}^e, e in [nl] (forward roots)
@@ -53,6 +55,7 @@ struct PhaseBFused {
     int64_t stride[FFTU_MAX_DIMS]; // element stride of axis l in the global array
     int P;                         // prod p_l
     int Mt;                        // consecutive m_d per tile
+    int lg_p[FFTU_MAX_DIMS], lg_L[FFTU_MAX_DIMS], lg_Mt;  // log2 of the power-of-two sizes
     int64_t tiles;
     int threads;
     double scale;

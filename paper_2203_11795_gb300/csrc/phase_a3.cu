@@ -43,13 +43,13 @@ namespace fftu {
 namespace {
 
 template <int N2_, int P2_, int R1_, int B_, int A_, int L0_, int Q1_, int W_, int MINB_, int NS_, bool PP_,
-          bool GT_ = false>
+          bool GT_ = false, int NT_ = 256>
 struct Cfg {
     static constexpr int N2 = N2_, P2 = P2_, L2 = N2 / P2, R1 = R1_, R2 = L2 / R1;
     static constexpr int B = B_, A = A_, L1 = A * B;
     static constexpr int L0 = L0_, Q1 = Q1_, Q2 = L0 / Q1;
     static constexpr int W = W_, NCH = N2 / W;
-    static constexpr int NT = 256;
+    static constexpr int NT = NT_;              // consumer threads (plus one producer warp)
     static constexpr int MINB = MINB_;          // resident CTAs per SM the register budget targets
     static constexpr int TILE1 = B * N2;        // stage-1 elements
     static constexpr int TILE2 = L0 * A * W;    // stage-2 elements
@@ -763,8 +763,11 @@ cudaError_t prepare_k(int n0, int n1, int *grids) {
 //                   {2, 3} buffers x {in place, ping-pong} x {2, 3} CTAs/SM)
 //   512^3, p = 4^3: L = 128, rows 128 = 8 x 16, axis 1 = 16 x 8, axis 0 = 8 x 16, W = 4;
 //                   two input buffers and a work buffer, 1 CTA/SM
+//   1024^3, p = 8^3: L = 128, rows 128 = 8 x 16, axis 1 = 8 x 16, axis 0 = 8 x 16, W = 4;
+//                   64 KB tiles, 512 consumer threads, 1 CTA/SM (residue units of 128 MiB: two kernels)
 using K512p8 = Cfg<512, 8, 8, 8, 8, 64, 8, 8, 2, 2, true, false>;
 using K512p4 = Cfg<512, 4, 8, 8, 16, 128, 8, 4, 1, 2, true>;
+using K1024p8 = Cfg<1024, 8, 8, 8, 16, 128, 8, 4, 1, 2, true, true, 512>;
 
 template <int DIR, bool PREP>
 cudaError_t dispatch(int which, const Phase3Launch *l, cudaStream_t st, int n0, int n1, int *grid, size_t *smem) {
@@ -775,6 +778,9 @@ cudaError_t dispatch(int which, const Phase3Launch *l, cudaStream_t st, int n0, 
         case 1:
             if (smem) *smem = pipe_smem_bytes<K512p4>(n0, n1);
             return PREP ? prepare_k<K512p4, DIR>(n0, n1, grid) : launch_k<K512p4, DIR>(*l, st);
+        case 2:
+            if (smem) *smem = pipe_smem_bytes<K1024p8>(n0, n1);
+            return PREP ? prepare_k<K1024p8, DIR>(n0, n1, grid) : launch_k<K1024p8, DIR>(*l, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -803,6 +809,10 @@ int phase_a3_select(int d, const int64_t *n, const int64_t *p, int is_double, Ph
     if (matches<K512p4>(n, p)) {
         fill<K512p4>(*info);
         return 1;
+    }
+    if (matches<K1024p8>(n, p)) {
+        fill<K1024p8>(*info);
+        return 2;
     }
     return -1;
 }
