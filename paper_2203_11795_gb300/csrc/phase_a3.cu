@@ -97,14 +97,14 @@ struct Tabs {
     float4 *tb;  // [k2][s2 / 2]: (w_{n2}^{k2 s2}, w_{n2}^{k2 (s2 + 1)})        stage 1b
     float2 *ta;  // [u][q]: w_{L2}^{q u}                                         stage 1a
     float2 *td;  // [u'][q']: w_{L0}^{q' u'}                                     stage 2b
-    float2 *t1;  // [e]: w_{n1}^e (read as a broadcast)                          stage 1c
-    float2 *tm;  // [e][k0]: w_{n0}^{k0 s0} w_{n1}^{k1 s1}, rebuilt per task     stage 2c
+    float2 *t1;  // [e]: w_{n1}^e (read as a broadcast)                          stages 1c, 2a
+    float2 *te;  // [s0][k0]: w_{n0}^{k0 s0}                                     stage 2c
     float2 *tile;
 };
 
 template <class K>
 __host__ __device__ constexpr size_t table_elems(int n0, int n1) {
-    return (size_t)K::L2 * K::P2 + K::R1 * K::R2 + K::Q1 * K::Q2 + (K::GLOBAL_T ? 0 : n1) + K::A * K::L0;
+    return (size_t)K::L2 * K::P2 + K::R1 * K::R2 + K::Q1 * K::Q2 + (K::GLOBAL_T ? 0 : n1 + n0);
 }
 
 template <class K, int DIR>
@@ -115,7 +115,7 @@ __device__ __forceinline__ Tabs build_tables(const Geo &g, unsigned char *raw) {
     T.ta = reinterpret_cast<float2 *>(T.tb + K::L2 * K::P2 / 2);
     T.td = T.ta + K::R1 * K::R2;
     T.t1 = T.td + K::Q1 * K::Q2;
-    T.tm = T.t1 + (K::GLOBAL_T ? 0 : g.n1);
+    T.te = T.t1 + (K::GLOBAL_T ? 0 : g.n1);
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int i = tid; i < K::L2 * K::P2 / 2; i += nt) {
         const int k2 = i / (K::P2 / 2), s2 = 2 * (i % (K::P2 / 2));
@@ -128,6 +128,10 @@ __device__ __forceinline__ Tabs build_tables(const Geo &g, unsigned char *raw) {
         T.td[i] = tw_at<DIR>(g.tw0, ((i % K::Q2) * (i / K::Q2) * g.P0) & (g.n0 - 1));
     if (!K::GLOBAL_T)
         for (int i = tid; i < g.n1; i += nt) T.t1[i] = tw_at<DIR>(g.tw1, i);
+    for (int i = tid; i < (K::GLOBAL_T ? 0 : g.n0); i += nt) {
+        const int s0 = i / K::L0, k0 = i % K::L0;
+        T.te[i] = tw_at<DIR>(g.tw0, (k0 * s0) & (g.n0 - 1));
+    }
     __syncthreads();
     return T;
 }
@@ -139,7 +143,11 @@ __device__ __forceinline__ float2 t1_at(const Geo &g, const Tabs &T, int e) {
     if constexpr (K::GLOBAL_T) return dirw<DIR>(__ldg(g.tw1 + e));
     return T.t1[e];
 }
-
+template <class K, int DIR>
+__device__ __forceinline__ float2 te_at(const Geo &g, const Tabs &T, int s0, int k0) {
+    if constexpr (K::GLOBAL_T) return dirw<DIR>(__ldg(g.tw0 + ((k0 * s0) & (g.n0 - 1))));
+    return T.te[s0 * K::L0 + k0];
+}
 
 // Scratch stores of the ring keep their lines in L2 (evict-last policy); the
 // stage-2 reader discards them after use so dead lines are never written back.
@@ -357,14 +365,7 @@ __device__ __forceinline__ void stage2_compute(const Geo &g, const Tabs &T, floa
                                                int c, int chunk) {
     const int tid = threadIdx.x;
     constexpr int HW = K::W / 2;
-    // The axis-1 twiddle w_{n1}^{k1 s1} does not depend on m0 or w, so it commutes with the axis-0
-    // sub-FFT; it is folded into the final twiddle: tm[e][k0] = w_{n0}^{k0 s0} w_{n1}^{(c + B e) s1}.
-    // (The previous task's last pass has finished reading tm: the caller's barrier separates tasks.)
-    for (int i = tid; i < K::A * K::L0; i += K::NT) {
-        const int e = i / K::L0, k0 = i % K::L0;
-        T.tm[i] = cmul(tw_at<DIR>(g.tw0, (k0 * s0) & (g.n0 - 1)), tw_at<DIR>(g.tw1, ((c + K::B * e) * s1) & (g.n1 - 1)));
-    }
-    // S2a (buf -> Y1): items (m0, w pair); F_A over a -> e (k1 = c + B e).
+    // S2a (buf -> Y1): items (m0, w pair); F_A over a -> e; k1 = c + B e; twiddle w_{n1}^{k1 s1}.
     // Y1 goes to `work` (ping-pong) or back into `buf`.
     float2 *y1 = K::PINGPONG ? work : buf;
     constexpr int IA = K::L0 * HW;
@@ -393,7 +394,10 @@ __device__ __forceinline__ void stage2_compute(const Geo &g, const Tabs &T, floa
             if (it < IA) {
                 const int wp = it % HW, m0 = it / HW;
 #pragma unroll
-                for (int e = 0; e < K::A; ++e) st_sh(y1 + (e * K::L0 + m0) * K::W + 2 * wp, ha[h][e], hb[h][e]);
+                for (int e = 0; e < K::A; ++e) {
+                    const float2 t = t1_at<K, DIR>(g, T, ((c + K::B * e) * s1) & (g.n1 - 1));
+                    st_sh(y1 + (e * K::L0 + m0) * K::W + 2 * wp, cmul(ha[h][e], t), cmul(hb[h][e], t));
+                }
             }
         }
     }
@@ -434,8 +438,7 @@ __device__ __forceinline__ void stage2_compute(const Geo &g, const Tabs &T, floa
         }
     }
     consumer_sync<K::NT>();
-    // S2c (buf -> HBM): items (e, u', w pair); F_{Q2} over q' -> v'; k0 = u' + Q1 v';
-    // twiddle w_{n0}^{k0 s0} w_{n1}^{k1 s1} from tm
+    // S2c (buf -> HBM): items (e, u', w pair); F_{Q2} over q' -> v'; k0 = u' + Q1 v'; twiddle w_{n0}^{k0 s0}
     constexpr int IC = K::A * K::Q1 * HW;
     for (int it = tid; it < IC; it += K::NT) {
         const int wp = it % HW, u = (it / HW) % K::Q1, e = it / (HW * K::Q1);
@@ -452,7 +455,7 @@ __device__ __forceinline__ void stage2_compute(const Geo &g, const Tabs &T, floa
 #pragma unroll
         for (int vv = 0; vv < K::Q2; ++vv) {
             const int k0 = u + K::Q1 * vv;
-            const float2 t = T.tm[e * K::L0 + k0];
+            const float2 t = te_at<K, DIR>(g, T, s0, k0);
             st_stream(dst + (size_t)(k0 + K::L0 * s0) * g.n1 * K::N2, cmul(va[vv], t), cmul(vb[vv], t));
         }
     }
@@ -517,7 +520,7 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
     const Tabs T =
         build_tables<K, DIR>(g, smem_raw + (size_t)(K::NS + (K::PINGPONG ? 1 : 0)) * K::TILE * sizeof(float2));
     uint64_t *full = reinterpret_cast<uint64_t *>(
-        (reinterpret_cast<uintptr_t>(T.tm + K::A * K::L0) + 7) & ~static_cast<uintptr_t>(7));
+        (reinterpret_cast<uintptr_t>(T.te + (K::GLOBAL_T ? 0 : g.n0)) + 7) & ~static_cast<uintptr_t>(7));
     uint64_t *empty = full + K::NS;
     int *task = reinterpret_cast<int *>(empty + K::NS);
     if (threadIdx.x == 0) {
