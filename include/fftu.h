@@ -141,6 +141,22 @@ fftu_status fftu_exec(fftu_handle plan, const void *in, void *out, void *stream)
 fftu_status fftu_exec_phase(fftu_handle plan, fftu_phase phase, const void *in, void *out,
                             void *stream);
 
+/*
+ * fftu_exec_pointwise -- out = inverse( forward(in) .* mul ), the transform pair with an elementwise
+ * product in between and no data reordering (Sec. 1.3: input and output share the distribution, so the
+ * inverse can follow the forward transform directly, with a local elementwise operation interspersed;
+ * Sec. 6: the split-step propagation of the time-dependent Schroedinger equation).
+ *   fwd, inv  plans of the same shape, cyclic grid, dtype and device; FFTU_FORWARD and FFTU_INVERSE.
+ *   in        device array of N elements (not modified unless it equals tmp).
+ *   mul       device array of N elements, the multiplier in the frequency domain, natural order.
+ *   tmp       device array of N elements for the spectrum; may equal in; must differ from out and mul.
+ *   out       device array of N elements; may equal in.
+ * When the forward plan's phase B is the fused 3D kernel, the product happens in its store (one extra
+ * read of mul, no extra pass); otherwise one elementwise pass follows phase B.  Stream-ordered.
+ */
+fftu_status fftu_exec_pointwise(fftu_handle fwd, fftu_handle inv, const void *in, const void *mul, void *tmp,
+                                void *out, void *stream);
+
 /* Free the plan's device memory and the handle.  Synchronises the device
  * with the plan's last use.  NULL is accepted. */
 fftu_status fftu_destroy(fftu_handle plan);

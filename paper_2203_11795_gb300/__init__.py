@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "FFTU_OK", 1: "FFTU_ERR_ARG", 2: "FFTU_ERR_DIVISIBILITY", 3: 
                 4: "FFTU_ERR_NOMEM", 5: "FFTU_ERR_CUDA", 6: "FFTU_ERR_TIMEOUT", 7: "FFTU_ERR_INTERNAL"}
 
 # Every entry point the header declares (checked by the test suite).
-EXPORTS = ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_destroy", "fftu_plan_info",
+EXPORTS = ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_exec_pointwise", "fftu_destroy",
+           "fftu_plan_info",
            "fftu_check_device_status", "fftu_exec_noalloc", "fftu_status_string", "fftu_last_error",
            "fftu_version")
 
@@ -64,6 +65,7 @@ def _load_library() -> ctypes.CDLL:
                                  ctypes.POINTER(fftu_options), ctypes.POINTER(h)]
     lib.fftu_exec.argtypes = [h, vp, vp, vp]
     lib.fftu_exec_phase.argtypes = [h, ctypes.c_int, vp, vp, vp]
+    lib.fftu_exec_pointwise.argtypes = [h, h, vp, vp, vp, vp, vp]
     lib.fftu_destroy.argtypes = [h]
     lib.fftu_plan_info.argtypes = [h, ctypes.POINTER(fftu_info)]
     lib.fftu_check_device_status.argtypes = [h]
@@ -72,7 +74,7 @@ def _load_library() -> ctypes.CDLL:
     lib.fftu_status_string.restype = ctypes.c_char_p
     lib.fftu_last_error.restype = ctypes.c_char_p
     lib.fftu_version.restype = ctypes.c_char_p
-    for name in ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_destroy",
+    for name in ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_exec_pointwise", "fftu_destroy",
                  "fftu_plan_info", "fftu_check_device_status", "fftu_exec_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
@@ -127,6 +129,12 @@ def fftu_exec(plan: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
 
 def fftu_exec_phase(plan: int, phase: int, in_ptr, out_ptr: int, stream: int = 0) -> None:
     _check(_lib.fftu_exec_phase(plan, int(phase), in_ptr, out_ptr, stream or None), "fftu_exec_phase")
+
+
+def fftu_exec_pointwise(fwd: int, inv: int, in_ptr: int, mul_ptr: int, tmp_ptr: int, out_ptr: int,
+                        stream: int = 0) -> None:
+    _check(_lib.fftu_exec_pointwise(fwd, inv, in_ptr, mul_ptr, tmp_ptr, out_ptr, stream or None),
+           "fftu_exec_pointwise")
 
 
 def fftu_destroy(plan: int) -> None:

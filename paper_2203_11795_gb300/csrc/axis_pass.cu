@@ -178,6 +178,12 @@ __global__ void twiddle_table_kernel(C *dst, int64_t n) {
     }
 }
 
+template <typename C>
+__global__ void pointwise_kernel(C *out, const C *mul, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = cmul(out[i], mul[i]);
+}
+
 template <typename C, int DIR>
 cudaError_t launch_axis_t(const AxisPass &a, cudaStream_t st) {
     size_t smem = (size_t)a.tile * sizeof(C);
@@ -221,6 +227,19 @@ cudaError_t launch_axis_pass(const AxisPass &a, int is_double, int dir, cudaStre
 cudaError_t prepare_axis_pass(int is_double, int dir) {
     if (is_double) return dir < 0 ? prepare_axis_t<double2, -1>() : prepare_axis_t<double2, 1>();
     return dir < 0 ? prepare_axis_t<float2, -1>() : prepare_axis_t<float2, 1>();
+}
+
+cudaError_t launch_pointwise(void *out, const void *mul, int64_t n, int is_double, cudaStream_t st) {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    if (is_double)
+        pointwise_kernel<double2><<<(unsigned)blocks, 256, 0, st>>>(static_cast<double2 *>(out),
+                                                                     static_cast<const double2 *>(mul), n);
+    else
+        pointwise_kernel<float2><<<(unsigned)blocks, 256, 0, st>>>(static_cast<float2 *>(out),
+                                                                    static_cast<const float2 *>(mul), n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_twiddle_table(void *dst, int64_t n, int is_double, cudaStream_t st) {

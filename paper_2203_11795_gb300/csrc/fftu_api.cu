@@ -357,7 +357,7 @@ void free_plan(Plan *pl) {
 }
 
 fftu_status run_steps(Plan *pl, const std::vector<Step> &steps, const void *first_src, void *dst,
-                      cudaStream_t st) {
+                      cudaStream_t st, const void *mul = nullptr) {
     const int is_double = pl->dtype == FFTU_C128;
     const void *src = first_src;
     if (steps.empty() && src != dst) {  // N = 1 or all n_l = 1: the transform is the identity
@@ -379,6 +379,8 @@ fftu_status run_steps(Plan *pl, const std::vector<Step> &steps, const void *firs
         } else if (s.kind == STEP_PHASE_B3) {
             PhaseBFused b = s.pb;
             b.data = dst;
+            b.mul = mul;
+            mul = nullptr;  // consumed by the fused store
             e = launch_phase_b3(b, is_double, pl->dir, st);
         } else {
             PhaseBFused b = s.pb;
@@ -387,6 +389,10 @@ fftu_status run_steps(Plan *pl, const std::vector<Step> &steps, const void *firs
         }
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         src = dst;
+    }
+    if (mul) {  // phase B could not fuse the multiply: one extra elementwise pass
+        cudaError_t e = launch_pointwise(dst, mul, pl->N, is_double, st);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     }
     return FFTU_OK;
 }
@@ -616,6 +622,58 @@ fftu_status fftu_exec_phase(fftu_handle h, fftu_phase phase, const void *in, voi
 
 fftu_status fftu_exec(fftu_handle h, const void *in, void *out, void *stream) {
     return fftu_exec_phase(h, FFTU_PHASE_ALL, in, out, stream);
+}
+
+fftu_status fftu_exec_pointwise(fftu_handle fwd, fftu_handle inv, const void *in, const void *mul, void *tmp,
+                                void *out, void *stream) {
+    using namespace fftu;
+    g_err[0] = '\0';
+    if (!fwd || !inv || !fwd->impl || !inv->impl) {
+        set_err("plans must be non-NULL");
+        return FFTU_ERR_ARG;
+    }
+    Plan *pf = fwd->impl, *pi = inv->impl;
+    if (pf->dir != FFTU_FORWARD || pi->dir != FFTU_INVERSE) {
+        set_err("fwd must be a forward plan and inv an inverse plan");
+        return FFTU_ERR_ARG;
+    }
+    bool same = pf->d == pi->d && pf->dtype == pi->dtype && pf->device == pi->device;
+    for (int l = 0; same && l < pf->d; ++l) same = pf->n[l] == pi->n[l] && pf->p[l] == pi->p[l];
+    if (!same) {
+        set_err("fwd and inv must have the same shape, cyclic grid, dtype and device");
+        return FFTU_ERR_ARG;
+    }
+    if (!in || !mul || !tmp || !out || tmp == out || mul == tmp) {
+        set_err("in, mul, tmp, out must be non-NULL; tmp must differ from out and mul");
+        return FFTU_ERR_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(mul) | reinterpret_cast<uintptr_t>(tmp) |
+         reinterpret_cast<uintptr_t>(out)) & 15) {
+        set_err("in/mul/tmp/out must be 16-byte aligned");
+        return FFTU_ERR_ARG;
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != pf->device) {
+        set_err("plan was made on device %d, current device is %d", pf->device, dev);
+        return FFTU_ERR_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // forward into tmp, the product fused into the forward phase B store
+    const bool ring_inplace = in == tmp && pf->phase_a.size() == 1 && pf->phase_a[0].kind == STEP_PHASE_A3 &&
+                              pf->phase_a[0].a3.mode == 1 && !pf->phase_a_inplace.empty();
+    fftu_status s = FFTU_OK;
+    if (pf->generic_pingpong) {
+        s = fftu_exec_phase(fwd, FFTU_PHASE_A, in, tmp, stream);
+    } else {
+        s = run_steps(pf, ring_inplace ? pf->phase_a_inplace : pf->phase_a, in, tmp, st);
+    }
+    if (s != FFTU_OK) return s;
+    s = run_steps(pf, pf->phase_b, tmp, tmp, st, mul);
+    if (s != FFTU_OK) return s;
+    // inverse from tmp into out (same distribution: no reordering in between)
+    return fftu_exec_phase(inv, FFTU_PHASE_ALL, tmp, out, stream);
 }
 
 fftu_status fftu_destroy(fftu_handle h) {

@@ -48,6 +48,7 @@ struct AxisPass {
 // Tile = all p values for Mt consecutive m along the last axis.
 struct PhaseBFused {
     void *data;
+    const void *mul;               // optional: output k is multiplied by mul[k] (natural index), else NULL
     int d;
     int64_t n[FFTU_MAX_DIMS];
     int64_t L[FFTU_MAX_DIMS];      // n_l / p_l
@@ -98,6 +99,8 @@ cudaError_t prepare_phase_b3(int is_double, int dir);
 int phase_b3_tile_mt(int P, int is_double);
 cudaError_t launch_phase_b3(const PhaseBFused &b, int is_double, int dir, cudaStream_t st);
 cudaError_t launch_twiddle_table(void *dst, int64_t n, int is_double, cudaStream_t st);
+// out[i] *= mul[i] for i in [n] (used when phase B cannot fuse the multiply).
+cudaError_t launch_pointwise(void *out, const void *mul, int64_t n, int is_double, cudaStream_t st);
 cudaError_t launch_axis_pass(const AxisPass &a, int is_double, int dir, cudaStream_t st);
 cudaError_t launch_phase_b_fused(const PhaseBFused &b, int is_double, int dir, cudaStream_t st);
 size_t axis_pass_smem_bytes(const AxisPass &a, int is_double);

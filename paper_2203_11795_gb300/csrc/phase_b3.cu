@@ -118,12 +118,19 @@ __global__ void __launch_bounds__(P0 * P1 * MT / 2) phase_b3_kernel(const __grid
             dft_small<P0, DIR>(va);
             dft_small<P0, DIR>(vb);
             C *dst = data + (base - 2 * hp + 2 * h) + k1 * L1 * st1 + k2 * L2;
+            const C *mul = static_cast<const C *>(b.mul);
 #pragma unroll
             for (int r = 0; r < P0; ++r) {
                 C a = va[r], c = vb[r];
                 if (b.scale != 1.0) {
                     a = cscale(a, scale);
                     c = cscale(c, scale);
+                }
+                if (mul) {  // pointwise product in the spectral domain, same natural index
+                    C ma, mc;
+                    load_pair(mul + (dst - data) + r * L0 * st0, ma, mc);
+                    a = cmul(a, ma);
+                    c = cmul(c, mc);
                 }
                 store_pair(dst + r * L0 * st0, a, c);
             }

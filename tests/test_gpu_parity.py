@@ -228,3 +228,40 @@ def test_full_size_1024_sampled(fftu, p):
     ref = oracle.dft_points(x, ks)
     # relative to the typical output magnitude sqrt(N) (Parseval), per point
     assert np.max(np.abs(got - ref)) / math.sqrt(N * 2.0 / 3.0) <= tol
+
+
+# ---- forward, pointwise product, inverse (no reordering in between) --------------------------
+
+@pytest.mark.parametrize("case", [((64, 64, 64), (4, 4, 4), np.complex64),      # product fused in phase B
+                                  ((512, 512, 512), (8, 8, 8), np.complex64),   # ring phase A + fused product
+                                  ((32, 16, 8), (2, 2, 2), np.complex128),      # separate product pass
+                                  ((256, 128), (4, 8), np.complex64)], ids=_id)
+@pytest.mark.parametrize("tmp_is_in", [False, True])
+def test_pointwise_convolution(fftu, case, tmp_is_in):
+    import torch
+    shape, p, dt = case
+    x = complex_uniform(909, shape, dtype=dt)
+    m = complex_uniform(910, shape, dtype=dt)
+    xt, mt = torch.from_numpy(x).cuda(), torch.from_numpy(m).cuda()
+    with fftu.Plan(shape, p, dtype=xt.dtype) as fwd, fftu.Plan(shape, p, dtype=xt.dtype, inverse=True) as inv:
+        tmp = xt.clone() if tmp_is_in else torch.empty_like(xt)
+        src = tmp if tmp_is_in else xt
+        out = torch.empty_like(xt)
+        fftu.fftu_exec_pointwise(fwd.handle, inv.handle, src.data_ptr(), mt.data_ptr(), tmp.data_ptr(),
+                                 out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+    x128 = x.astype(np.complex128)
+    ref = oracle.fftn(oracle.fftn(x128) * m.astype(np.complex128), inverse=True)
+    assert oracle.rel_l2(out.cpu().numpy(), ref) <= tolerance(dt, x.size)
+
+
+def test_pointwise_rejects_mismatched_plans(fftu):
+    import torch
+    x = torch.zeros((16, 16), dtype=torch.complex64, device="cuda")
+    with fftu.Plan((16, 16), (2, 2)) as fwd, fftu.Plan((16, 16), (4, 2), inverse=True) as inv, \
+            fftu.Plan((16, 16), (2, 2)) as fwd2:
+        for a, b in ((fwd, inv), (fwd, fwd2)):
+            with pytest.raises(fftu.FFTUError) as ei:
+                fftu.fftu_exec_pointwise(a.handle, b.handle, x.data_ptr(), x.data_ptr(), x.data_ptr() + 0,
+                                         x.data_ptr(), 0)
+            assert ei.value.status == 1
