@@ -192,6 +192,28 @@ fftu_status fftu_check_device_status(fftu_handle plan);
 fftu_status fftu_exec_noalloc(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,
                               const void *in, void *out, void *stream);
 
+/*
+ * Batches: many transforms of different shapes in one persistent kernel launch.
+ * fftu_batch_create -- build a batch from `count` (1..128) existing plans with the same dtype,
+ *   direction and device.  Every pass of every plan becomes a job (phase A's strided sub-FFT passes,
+ *   then phase B, Algorithm 2.3); a persistent kernel takes their tiles in pass-major order and a tile
+ *   of pass k waits (bounded) for pass k - 1 of the same transform.  Plans whose phase A alternates with
+ *   a workspace (a line longer than a tile) are not batched (FFTU_ERR_UNSUPPORTED).  The batch reads the
+ *   plans' twiddle tables: destroy the batch before its plans.  It owns a small device job table and
+ *   counters.
+ * fftu_batch_exec -- run the batch on `stream`: ins[i] -> outs[i] (device arrays of plan i's size,
+ *   16-byte aligned; outs[i] may equal ins[i]; arrays of different transforms must not overlap).  No host
+ *   synchronisation: the counters are cleared on the stream, so the call can be captured into a CUDA graph.
+ *   One batch may run on one stream at a time.
+ * fftu_batch_check_status -- read and clear the batch's device status word (bounded waits); synchronises.
+ * fftu_batch_destroy -- synchronise the device and free the batch (NULL accepted).
+ */
+typedef struct fftu_batch_st *fftu_batch;
+fftu_status fftu_batch_create(int count, const fftu_handle *plans, fftu_batch *out);
+fftu_status fftu_batch_exec(fftu_batch batch, const void *const *ins, void *const *outs, void *stream);
+fftu_status fftu_batch_check_status(fftu_batch batch);
+fftu_status fftu_batch_destroy(fftu_batch batch);
+
 /* Static string for a status code. */
 const char *fftu_status_string(fftu_status s);
 

@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "FFTU_OK", 1: "FFTU_ERR_ARG", 2: "FFTU_ERR_DIVISIBILITY", 3: 
 # Every entry point the header declares (checked by the test suite).
 EXPORTS = ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_exec_pointwise", "fftu_destroy",
            "fftu_plan_info",
-           "fftu_check_device_status", "fftu_exec_noalloc", "fftu_status_string", "fftu_last_error",
+           "fftu_check_device_status", "fftu_exec_noalloc", "fftu_batch_create", "fftu_batch_exec",
+           "fftu_batch_check_status", "fftu_batch_destroy", "fftu_status_string", "fftu_last_error",
            "fftu_version")
 
 
@@ -70,12 +71,17 @@ def _load_library() -> ctypes.CDLL:
     lib.fftu_plan_info.argtypes = [h, ctypes.POINTER(fftu_info)]
     lib.fftu_check_device_status.argtypes = [h]
     lib.fftu_exec_noalloc.argtypes = [ctypes.c_int, i64p, i64p, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+    lib.fftu_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(h), ctypes.POINTER(h)]
+    lib.fftu_batch_exec.argtypes = [h, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    lib.fftu_batch_check_status.argtypes = [h]
+    lib.fftu_batch_destroy.argtypes = [h]
     lib.fftu_status_string.argtypes = [ctypes.c_int]
     lib.fftu_status_string.restype = ctypes.c_char_p
     lib.fftu_last_error.restype = ctypes.c_char_p
     lib.fftu_version.restype = ctypes.c_char_p
     for name in ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_exec_pointwise", "fftu_destroy",
-                 "fftu_plan_info", "fftu_check_device_status", "fftu_exec_noalloc"):
+                 "fftu_plan_info", "fftu_check_device_status", "fftu_exec_noalloc", "fftu_batch_create",
+                 "fftu_batch_exec", "fftu_batch_check_status", "fftu_batch_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -160,6 +166,27 @@ def fftu_exec_noalloc(d: int, n, p, dtype: int, direction: int, in_ptr: int, out
     """Whole transform with no device allocation (static device scratch); see include/fftu.h."""
     _check(_lib.fftu_exec_noalloc(int(d), _i64(n), _i64(p), int(dtype), int(direction), in_ptr, out_ptr,
                                   stream or None), "fftu_exec_noalloc")
+
+
+def fftu_batch_create(plans) -> int:
+    hs = (ctypes.c_void_p * len(plans))(*plans)
+    b = ctypes.c_void_p()
+    _check(_lib.fftu_batch_create(len(plans), hs, ctypes.byref(b)), "fftu_batch_create")
+    return b.value
+
+
+def fftu_batch_exec(batch: int, in_ptrs, out_ptrs, stream: int = 0) -> None:
+    ins = (ctypes.c_void_p * len(in_ptrs))(*in_ptrs)
+    outs = (ctypes.c_void_p * len(out_ptrs))(*out_ptrs)
+    _check(_lib.fftu_batch_exec(batch, ins, outs, stream or None), "fftu_batch_exec")
+
+
+def fftu_batch_check_status(batch: int) -> None:
+    _check(_lib.fftu_batch_check_status(batch), "fftu_batch_check_status")
+
+
+def fftu_batch_destroy(batch: int) -> None:
+    _check(_lib.fftu_batch_destroy(batch), "fftu_batch_destroy")
 
 
 def fftu_status_string(status: int) -> str:

@@ -19,71 +19,13 @@
 
 #include "fft_device.cuh"
 #include "fftu_internal.h"
+#include "generic_tiles.cuh"
 
 namespace fftu {
 
 namespace {
 
-// complex values a thread holds per stage: 16 (c64) or 8 (c128)
-template <typename C> __host__ __device__ constexpr int ept() { return sizeof(C) == 8 ? kEptMax : kEptMax / 2; }
 constexpr int kAxisThreads = 512;
-
-template <typename C, int DIR, int R>
-__device__ __forceinline__ void stockham_stage(C *sm, const C *__restrict__ tw, const AxisPass &a, int Ns,
-                                               int tid, int nthreads) {
-    constexpr int B = ept<C>() / R > 0 ? ept<C>() / R : 1;  // butterflies per thread per stage
-    const int lg_cols = a.lg_Gt + a.lg_V;
-    const int cols = 1 << lg_cols;
-    const int per_col = a.len / R;
-    const int total = cols * per_col;
-    const int twstep = a.nl / (Ns * R);
-    const int lg_ns = 31 - __clz(Ns);
-    C v[B][R];
-#pragma unroll
-    for (int q = 0; q < B; ++q) {
-        const int w = tid + q * nthreads;
-        if (w < total) {
-            const int col = w & (cols - 1), b = w >> lg_cols;
-            int base, js;
-            if (a.contiguous) {
-                base = ((col >> a.lg_Gt) << a.lg_nlt) + (col & (a.Gt - 1));
-                js = a.Gt;
-            } else {
-                base = col;
-                js = cols;
-            }
-            const int k = b & (Ns - 1);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                C x = sm[base + (b + r * per_col) * js];
-                if (r > 0 && Ns > 1) x = cmul(x, dirw<DIR>(tw[r * k * twstep]));
-                v[q][r] = x;
-            }
-            dft_small<R, DIR>(v[q]);
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < B; ++q) {
-        const int w = tid + q * nthreads;
-        if (w < total) {
-            const int col = w & (cols - 1), b = w >> lg_cols;
-            int base, js;
-            if (a.contiguous) {
-                base = ((col >> a.lg_Gt) << a.lg_nlt) + (col & (a.Gt - 1));
-                js = a.Gt;
-            } else {
-                base = col;
-                js = cols;
-            }
-            const int k = b & (Ns - 1);
-            const int o = ((b >> lg_ns) << lg_ns) * R + k;
-#pragma unroll
-            for (int r = 0; r < R; ++r) sm[base + (o + r * Ns) * js] = v[q][r];
-        }
-    }
-    __syncthreads();
-}
 
 // R0: radix of the first stage (1 = none); every later stage is radix 8.
 template <typename C, int DIR, int R0>
@@ -93,75 +35,7 @@ __global__ void __launch_bounds__(kAxisThreads) axis_pass_kernel(const __grid_co
     const C *__restrict__ src = static_cast<const C *>(a.src);
     C *__restrict__ dst = static_cast<C *>(a.dst);
     const C *__restrict__ tw = static_cast<const C *>(a.tw);
-    using Rl = typename real_of<C>::type;
-    const int tid = threadIdx.x, nt = blockDim.x;
-
-    const int chunks = 1 << a.lg_chunks;  // class chunks per line
-    for (int64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) {
-        const int cc = (int)(t & (chunks - 1));
-        const int64_t tt = t >> a.lg_chunks;
-        const int c0 = cc << a.lg_Gt;
-        int64_t gbase;  // element offset of (first line or vector, line position 0)
-        if (a.contiguous) {
-            gbase = (tt << a.lg_V) * a.nl;
-        } else {
-            const int64_t tpo_mask = ((int64_t)1 << a.lg_tpo) - 1;
-            gbase = (tt >> a.lg_tpo) * (int64_t)a.nl * a.inner + ((tt & tpo_mask) << a.lg_V);
-        }
-        // load: shared index e is the natural order of the tile (tile line position lp, vector v);
-        // tile position lp = c_local + j Gt holds line position c0 + c_local + j G
-        for (int e = tid; e < a.tile; e += nt) {
-            int lp, v;
-            if (a.contiguous) {
-                v = e >> a.lg_nlt;
-                lp = e & (a.nlt - 1);
-            } else {
-                lp = e >> a.lg_V;
-                v = e & (a.V - 1);
-            }
-            const int64_t gp = c0 + (lp & (a.Gt - 1)) + ((int64_t)(lp >> a.lg_Gt) << a.lg_G);
-            const int64_t g = a.contiguous ? gbase + (int64_t)v * a.nl + gp : gbase + gp * a.inner + v;
-            sm[e] = src[g];
-        }
-        __syncthreads();
-
-        int Ns = 1;
-        if constexpr (R0 > 1) {
-            stockham_stage<C, DIR, R0>(sm, tw, a, Ns, tid, nt);
-            Ns = R0;
-        }
-        for (; Ns < a.len; Ns *= 8) stockham_stage<C, DIR, 8>(sm, tw, a, Ns, tid, nt);
-
-        // store with the output permutation, twiddle and scale
-        const Rl scale = (Rl)a.scale;
-        for (int e = tid; e < a.tile; e += nt) {
-            int lpo, v;  // tile output position and vector
-            if (a.contiguous) {
-                v = e >> a.lg_nlt;
-                lpo = e & (a.nlt - 1);
-            } else {
-                lpo = e >> a.lg_V;
-                v = e & (a.V - 1);
-            }
-            C val;
-            int64_t gp;  // global line position of the output
-            if (a.mode == 0) {
-                const int cl = lpo >> a.lg_len, m = lpo & (a.len - 1);
-                const int c = c0 + cl;
-                const int src_lp = cl + (m << a.lg_Gt);
-                val = sm[a.contiguous ? (v << a.lg_nlt) + src_lp : (src_lp << a.lg_V) + v];
-                if (c != 0 && m != 0) val = cmul(val, dirw<DIR>(tw[c * m]));
-                gp = ((int64_t)c << a.lg_len) + m;
-            } else {
-                val = sm[e];
-                gp = c0 + (lpo & (a.Gt - 1)) + ((int64_t)(lpo >> a.lg_Gt) << a.lg_G);
-            }
-            if (a.scale != 1.0) val = cscale(val, scale);
-            const int64_t g = a.contiguous ? gbase + (int64_t)v * a.nl + gp : gbase + gp * a.inner + v;
-            dst[g] = val;
-        }
-        __syncthreads();
-    }
+    for (int64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) axis_tile<C, DIR, R0>(a, t, sm, src, dst, tw);
 }
 
 // w_n^e = exp(-2 pi i e / n) for e in [n], evaluated in FP64 by sincospi on the

@@ -407,6 +407,49 @@ struct fftu_plan_st {
     Plan *impl;
 };
 
+namespace fftu {
+
+fftu_status plan_view(fftu_handle h, PlanView *v) {
+    if (!h || !h->impl) {
+        record_error("batch: NULL plan");
+        return FFTU_ERR_ARG;
+    }
+    const Plan &pl = *h->impl;
+    v->dtype = pl.dtype;
+    v->dir = pl.dir;
+    v->device = pl.device;
+    v->pingpong = pl.generic_pingpong;
+    v->a_passes.clear();
+    v->b_steps.clear();
+    const bool fused_a = !pl.phase_a.empty() && pl.phase_a[0].kind == STEP_PHASE_A3;
+    for (const Step &s : fused_a ? pl.phase_a_inplace : pl.phase_a) {
+        StepView sv;
+        std::memset(&sv, 0, sizeof(sv));
+        sv.is_axis = true;
+        sv.axis = s.axis;
+        v->a_passes.push_back(sv);
+    }
+    const double scale = pl.dir == FFTU_INVERSE ? 1.0 / (double)pl.N : 1.0;
+    for (const Step &s : pl.phase_b) {
+        StepView sv;
+        std::memset(&sv, 0, sizeof(sv));
+        if (s.kind == STEP_AXIS) {
+            sv.is_axis = true;
+            sv.axis = s.axis;
+        } else {
+            sv.is_axis = false;
+            if (!make_phase_b_fused(pl, scale, sv.pb)) {  // the generic form of the fused phase B
+                record_error("batch: phase B has no generic fused form");
+                return FFTU_ERR_UNSUPPORTED;
+            }
+        }
+        v->b_steps.push_back(sv);
+    }
+    return FFTU_OK;
+}
+
+}  // namespace fftu
+
 extern "C" {
 
 fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,

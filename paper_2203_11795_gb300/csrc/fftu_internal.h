@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/fftu.h"
 
 namespace fftu {
@@ -85,6 +87,21 @@ cudaError_t prepare_phase_a3(int which, int dir, int n0, int n1, int *grids, siz
 cudaError_t launch_phase_a3(const Phase3Launch &l, cudaStream_t st);
 
 struct Plan;
+
+// A plan seen as a list of generic passes (for batching many plans in one launch).
+constexpr int kMaxBatch = 128;
+struct StepView {
+    bool is_axis;
+    AxisPass axis;   // is_axis: a strided sub-FFT pass (mode 0 or 1)
+    PhaseBFused pb;  // otherwise: the generic fused phase B
+};
+struct PlanView {
+    int dtype, dir, device;
+    bool pingpong;                  // phase A alternates with a workspace (long lines)
+    std::vector<StepView> a_passes;  // phase A, generic passes (first reads in, then in place on out)
+    std::vector<StepView> b_steps;   // phase B, in place on out
+};
+fftu_status plan_view(fftu_handle h, PlanView *v);
 
 // Set the calling thread's detail string returned by fftu_last_error().
 void record_error(const char *msg);

@@ -1,0 +1,217 @@
+// Per-tile bodies of the generic kernels, shared by the one-pass-per-launch kernels
+// (axis_pass.cu, phase_b.cu) and the persistent batch kernel (batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fft_device.cuh"
+#include "fftu_internal.h"
+
+namespace fftu {
+
+// complex values a thread holds per stage: 16 (c64) or 8 (c128)
+template <typename C> __host__ __device__ constexpr int ept() { return sizeof(C) == 8 ? kEptMax : kEptMax / 2; }
+
+
+template <typename C, int DIR, int R>
+__device__ __forceinline__ void stockham_stage(C *sm, const C *__restrict__ tw, const AxisPass &a, int Ns,
+                                               int tid, int nthreads) {
+    constexpr int B = ept<C>() / R > 0 ? ept<C>() / R : 1;  // butterflies per thread per stage
+    const int lg_cols = a.lg_Gt + a.lg_V;
+    const int cols = 1 << lg_cols;
+    const int per_col = a.len / R;
+    const int total = cols * per_col;
+    const int twstep = a.nl / (Ns * R);
+    const int lg_ns = 31 - __clz(Ns);
+    C v[B][R];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        const int w = tid + q * nthreads;
+        if (w < total) {
+            const int col = w & (cols - 1), b = w >> lg_cols;
+            int base, js;
+            if (a.contiguous) {
+                base = ((col >> a.lg_Gt) << a.lg_nlt) + (col & (a.Gt - 1));
+                js = a.Gt;
+            } else {
+                base = col;
+                js = cols;
+            }
+            const int k = b & (Ns - 1);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                C x = sm[base + (b + r * per_col) * js];
+                if (r > 0 && Ns > 1) x = cmul(x, dirw<DIR>(tw[r * k * twstep]));
+                v[q][r] = x;
+            }
+            dft_small<R, DIR>(v[q]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        const int w = tid + q * nthreads;
+        if (w < total) {
+            const int col = w & (cols - 1), b = w >> lg_cols;
+            int base, js;
+            if (a.contiguous) {
+                base = ((col >> a.lg_Gt) << a.lg_nlt) + (col & (a.Gt - 1));
+                js = a.Gt;
+            } else {
+                base = col;
+                js = cols;
+            }
+            const int k = b & (Ns - 1);
+            const int o = ((b >> lg_ns) << lg_ns) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm[base + (o + r * Ns) * js] = v[q][r];
+        }
+    }
+    __syncthreads();
+}
+
+// One tile of a generic strided pass (see AxisPass): load, Stockham stages, permuted store.
+template <typename C, int DIR, int R0>
+__device__ __forceinline__ void axis_tile(const AxisPass &a, int64_t t, C *sm, const C *__restrict__ src,
+                                          C *__restrict__ dst, const C *__restrict__ tw) {
+    using Rl = typename real_of<C>::type;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int chunks = 1 << a.lg_chunks;  // class chunks per line
+    const int cc = (int)(t & (chunks - 1));
+    const int64_t tt = t >> a.lg_chunks;
+    const int c0 = cc << a.lg_Gt;
+    int64_t gbase;  // element offset of (first line or vector, line position 0)
+    if (a.contiguous) {
+        gbase = (tt << a.lg_V) * a.nl;
+    } else {
+        const int64_t tpo_mask = ((int64_t)1 << a.lg_tpo) - 1;
+        gbase = (tt >> a.lg_tpo) * (int64_t)a.nl * a.inner + ((tt & tpo_mask) << a.lg_V);
+    }
+    // load: shared index e is the natural order of the tile (tile line position lp, vector v);
+    // tile position lp = c_local + j Gt holds line position c0 + c_local + j G
+    for (int e = tid; e < a.tile; e += nt) {
+        int lp, v;
+        if (a.contiguous) {
+            v = e >> a.lg_nlt;
+            lp = e & (a.nlt - 1);
+        } else {
+            lp = e >> a.lg_V;
+            v = e & (a.V - 1);
+        }
+        const int64_t gp = c0 + (lp & (a.Gt - 1)) + ((int64_t)(lp >> a.lg_Gt) << a.lg_G);
+        const int64_t g = a.contiguous ? gbase + (int64_t)v * a.nl + gp : gbase + gp * a.inner + v;
+        sm[e] = src[g];
+    }
+    __syncthreads();
+
+    int Ns = 1;
+    if constexpr (R0 > 1) {
+        stockham_stage<C, DIR, R0>(sm, tw, a, Ns, tid, nt);
+        Ns = R0;
+    }
+    for (; Ns < a.len; Ns *= 8) stockham_stage<C, DIR, 8>(sm, tw, a, Ns, tid, nt);
+
+    // store with the output permutation, twiddle and scale
+    const Rl scale = (Rl)a.scale;
+    for (int e = tid; e < a.tile; e += nt) {
+        int lpo, v;  // tile output position and vector
+        if (a.contiguous) {
+            v = e >> a.lg_nlt;
+            lpo = e & (a.nlt - 1);
+        } else {
+            lpo = e >> a.lg_V;
+            v = e & (a.V - 1);
+        }
+        C val;
+        int64_t gp;  // global line position of the output
+        if (a.mode == 0) {
+            const int cl = lpo >> a.lg_len, m = lpo & (a.len - 1);
+            const int c = c0 + cl;
+            const int src_lp = cl + (m << a.lg_Gt);
+            val = sm[a.contiguous ? (v << a.lg_nlt) + src_lp : (src_lp << a.lg_V) + v];
+            if (c != 0 && m != 0) val = cmul(val, dirw<DIR>(tw[c * m]));
+            gp = ((int64_t)c << a.lg_len) + m;
+        } else {
+            val = sm[e];
+            gp = c0 + (lpo & (a.Gt - 1)) + ((int64_t)(lpo >> a.lg_Gt) << a.lg_G);
+        }
+        if (a.scale != 1.0) val = cscale(val, scale);
+        const int64_t g = a.contiguous ? gbase + (int64_t)v * a.nl + gp : gbase + gp * a.inner + v;
+        dst[g] = val;
+    }
+    __syncthreads();
+}
+
+template <typename C, int DIR, int R>
+__device__ __forceinline__ void axis_dft(C *sm, int total, int S, int tid, int nt) {
+    // groups: total / R, group g -> base (g / S) * S * R + g % S, stride S (S a power of two)
+    const int groups = total / R;
+    const int lg_s = 31 - __clz(S);
+    for (int g = tid; g < groups; g += nt) {
+        const int base = ((g >> lg_s) << lg_s) * R + (g & (S - 1));
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = sm[base + r * S];
+        dft_small<R, DIR>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[base + r * S] = v[r];
+    }
+}
+
+// One tile of the generic fused phase B (see PhaseBFused): all p values for Mt consecutive m_d.
+template <typename C, int DIR>
+__device__ __forceinline__ void phaseb_tile(const PhaseBFused &b, int64_t t, C *sm, C *__restrict__ data) {
+    using Rl = typename real_of<C>::type;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int d = b.d;
+    const int total = b.P * b.Mt;
+    const int lg_td = b.lg_L[d - 1] - b.lg_Mt;  // tiles along the last axis (log2)
+    // tile -> fixed m_0..m_{d-2} and the first m_{d-1}
+    int64_t rem = t >> lg_td;
+    int64_t base = ((t & (((int64_t)1 << lg_td) - 1)) << b.lg_Mt) * b.stride[d - 1];
+    for (int l = d - 2; l >= 0; --l) {
+        base += (rem & (b.L[l] - 1)) * b.stride[l];
+        rem >>= b.lg_L[l];
+    }
+    for (int e = tid; e < total; e += nt) {
+        const int mt = e & (b.Mt - 1);
+        int sf = e >> b.lg_Mt;
+        int64_t g = base + (int64_t)mt * b.stride[d - 1];
+        for (int l = d - 1; l >= 0; --l) {
+            const int sl = sf & (b.p[l] - 1);
+            sf >>= b.lg_p[l];
+            g += (int64_t)sl * b.L[l] * b.stride[l];
+        }
+        sm[e] = data[g];
+    }
+    __syncthreads();
+    int S = b.Mt;
+    for (int l = d - 1; l >= 0; --l) {
+        switch (b.p[l]) {
+            case 2: axis_dft<C, DIR, 2>(sm, total, S, tid, nt); break;
+            case 4: axis_dft<C, DIR, 4>(sm, total, S, tid, nt); break;
+            case 8: axis_dft<C, DIR, 8>(sm, total, S, tid, nt); break;
+            case 16: axis_dft<C, DIR, 16>(sm, total, S, tid, nt); break;
+            default: break;
+        }
+        S *= b.p[l];
+        __syncthreads();
+    }
+    const Rl scale = (Rl)b.scale;
+    for (int e = tid; e < total; e += nt) {
+        const int mt = e & (b.Mt - 1);
+        int sf = e >> b.lg_Mt;
+        int64_t g = base + (int64_t)mt * b.stride[d - 1];
+        for (int l = d - 1; l >= 0; --l) {
+            const int sl = sf & (b.p[l] - 1);
+            sf >>= b.lg_p[l];
+            g += (int64_t)sl * b.L[l] * b.stride[l];
+        }
+        C v = sm[e];
+        if (b.scale != 1.0) v = cscale(v, scale);
+        data[g] = v;
+    }
+    __syncthreads();
+}
+
+}  // namespace fftu

@@ -16,86 +16,18 @@
 
 #include "fft_device.cuh"
 #include "fftu_internal.h"
+#include "generic_tiles.cuh"
 
 namespace fftu {
 
 namespace {
-
-template <typename C, int DIR, int R>
-__device__ __forceinline__ void axis_dft(C *sm, int total, int S, int tid, int nt) {
-    // groups: total / R, group g -> base (g / S) * S * R + g % S, stride S (S a power of two)
-    const int groups = total / R;
-    const int lg_s = 31 - __clz(S);
-    for (int g = tid; g < groups; g += nt) {
-        const int base = ((g >> lg_s) << lg_s) * R + (g & (S - 1));
-        C v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = sm[base + r * S];
-        dft_small<R, DIR>(v);
-#pragma unroll
-        for (int r = 0; r < R; ++r) sm[base + r * S] = v[r];
-    }
-}
 
 template <typename C, int DIR>
 __global__ void __launch_bounds__(256) phase_b_fused_kernel(const __grid_constant__ PhaseBFused b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
     C *__restrict__ data = static_cast<C *>(b.data);
-    using Rl = typename real_of<C>::type;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int d = b.d;
-    const int total = b.P * b.Mt;
-    const int lg_td = b.lg_L[d - 1] - b.lg_Mt;  // tiles along the last axis (log2)
-
-    for (int64_t t = blockIdx.x; t < b.tiles; t += gridDim.x) {
-        // tile -> fixed m_0..m_{d-2} and the first m_{d-1}
-        int64_t rem = t >> lg_td;
-        int64_t base = ((t & (((int64_t)1 << lg_td) - 1)) << b.lg_Mt) * b.stride[d - 1];
-        for (int l = d - 2; l >= 0; --l) {
-            base += (rem & (b.L[l] - 1)) * b.stride[l];
-            rem >>= b.lg_L[l];
-        }
-        for (int e = tid; e < total; e += nt) {
-            const int mt = e & (b.Mt - 1);
-            int sf = e >> b.lg_Mt;
-            int64_t g = base + (int64_t)mt * b.stride[d - 1];
-            for (int l = d - 1; l >= 0; --l) {
-                const int sl = sf & (b.p[l] - 1);
-                sf >>= b.lg_p[l];
-                g += (int64_t)sl * b.L[l] * b.stride[l];
-            }
-            sm[e] = data[g];
-        }
-        __syncthreads();
-        int S = b.Mt;
-        for (int l = d - 1; l >= 0; --l) {
-            switch (b.p[l]) {
-                case 2: axis_dft<C, DIR, 2>(sm, total, S, tid, nt); break;
-                case 4: axis_dft<C, DIR, 4>(sm, total, S, tid, nt); break;
-                case 8: axis_dft<C, DIR, 8>(sm, total, S, tid, nt); break;
-                case 16: axis_dft<C, DIR, 16>(sm, total, S, tid, nt); break;
-                default: break;
-            }
-            S *= b.p[l];
-            __syncthreads();
-        }
-        const Rl scale = (Rl)b.scale;
-        for (int e = tid; e < total; e += nt) {
-            const int mt = e & (b.Mt - 1);
-            int sf = e >> b.lg_Mt;
-            int64_t g = base + (int64_t)mt * b.stride[d - 1];
-            for (int l = d - 1; l >= 0; --l) {
-                const int sl = sf & (b.p[l] - 1);
-                sf >>= b.lg_p[l];
-                g += (int64_t)sl * b.L[l] * b.stride[l];
-            }
-            C v = sm[e];
-            if (b.scale != 1.0) v = cscale(v, scale);
-            data[g] = v;
-        }
-        __syncthreads();
-    }
+    for (int64_t t = blockIdx.x; t < b.tiles; t += gridDim.x) phaseb_tile<C, DIR>(b, t, sm, data);
 }
 
 template <typename C, int DIR>
