@@ -42,7 +42,10 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--shape", default="512,512,512")
-    ap.add_argument("--p", default="8,8,8")
+    ap.add_argument("--p", default="8,8,8", help="cyclic grid, or 'tune' to let the plan-time tuner choose")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="K > 0: time K uneven 3D transforms (n_l in {32, 64, 128}) in one persistent launch "
+                         "per direction instead of the single-array workload")
     ap.add_argument("--schedule", type=int, default=0, help="0 auto, 1 generic, 2 fused")
     ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
     ap.add_argument("--seed", type=int, default=2024)
@@ -193,7 +196,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{'x'.join(map(str, shape))} complex64 forward+inverse FFT",
-                   "shape": list(shape), "p": list(shape_of(args.p))},
+                   "shape": list(shape), "p": args.p if args.p == "tune" else list(shape_of(args.p))},
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
                          "sample": f"FP64 oracle forward+inverse of a {'x'.join(map(str, sample))} sample "
                                    f"per step (seeded uniform inputs), GB/s scaled by the sample's 4*N*8 bytes"},
@@ -218,7 +221,9 @@ def run_ours(args):
     import paper_2203_11795_gb300 as fftu
     from fftu_inputs import complex_uniform
 
-    shape, p = shape_of(args.shape), shape_of(args.p)
+    shape = shape_of(args.shape)
+    tune = args.p == "tune"
+    p = None if tune else shape_of(args.p)
     N = math.prod(shape)
     np_dtype, t_dtype = (np.complex64, torch.complex64) if args.dtype == "c64" else (np.complex128, torch.complex128)
     esize = 8 if args.dtype == "c64" else 16
@@ -226,8 +231,12 @@ def run_ours(args):
     x = x_host.to(dev)
     y = torch.empty_like(x)
     z = torch.empty_like(x)
-    fwd = fftu.Plan(shape, p, dtype=t_dtype, schedule=args.schedule)
-    inv = fftu.Plan(shape, p, dtype=t_dtype, inverse=True, schedule=args.schedule)
+    t_plan = time.perf_counter()
+    fwd = fftu.Plan(shape, p, dtype=t_dtype, schedule=args.schedule, tune=tune)
+    inv = fftu.Plan(shape, p, dtype=t_dtype, inverse=True, schedule=args.schedule, tune=tune)
+    t_plan = time.perf_counter() - t_plan
+    if tune:
+        p = tuple(fwd.info["p"])
     stream = torch.cuda.Stream(dev)
     sh = stream.cuda_stream
     A, B = fftu.FFTU_PHASE_A, fftu.FFTU_PHASE_B
@@ -334,8 +343,9 @@ def run_ours(args):
             "dtype": "f32" if esize == 8 else "f64", "data": "synthetic",
             "config": {"workload": f"{'x'.join(map(str, shape))} complex{'64' if esize == 8 else '128'} "
                                    f"forward+inverse FFT, cyclic "
-                                   f"p={'x'.join(map(str, p))}",
+                                   f"p={'x'.join(map(str, p))}" + (" (tuned)" if tune else ""),
                        "shape": list(shape), "p": list(p), "schedule": fwd.info["schedule"],
+                       "p_inverse": inv.info["p"], "tuned": tune, "plan_seconds": t_plan,
                        "l2": ("inputs larger than L2 (129 MB); no flush" if N * esize > 129e6 else
                               "inputs smaller than L2: L2-resident, not an HBM measurement"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -354,10 +364,152 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def uneven_shapes(count, seed):
+    """Each n_l drawn independently from {32, 64, 128}: sizes 32^3 to 128^3, cubes included."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    return [tuple(int(v) for v in rng.choice([32, 64, 128], size=3)) for _ in range(count)]
+
+
+def run_batch(args):
+    """K uneven complex64 3D transforms, forward then inverse, each direction one persistent launch."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2203_11795_gb300 import _build
+    _build.build()
+    import paper_2203_11795_gb300 as fftu
+    from fftu_inputs import complex_uniform
+
+    shapes = uneven_shapes(args.batch, args.seed)
+    hosts = [torch.from_numpy(complex_uniform(args.seed + 1000 * rank + i, s, dtype=np.complex64)).pin_memory()
+             for i, s in enumerate(shapes)]
+    xs = [h.to(dev) for h in hosts]
+    ys = [torch.empty_like(x) for x in xs]
+    zs = [torch.empty_like(x) for x in xs]
+    fwd = [fftu.Plan(s, None, dtype=torch.complex64) for s in shapes]
+    inv = [fftu.Plan(s, None, dtype=torch.complex64, inverse=True) for s in shapes]
+    bf = fftu.fftu_batch_create([q.handle for q in fwd])
+    bi = fftu.fftu_batch_create([q.handle for q in inv])
+    px, py, pz = ([t.data_ptr() for t in ts] for ts in (xs, ys, zs))
+    stream = torch.cuda.Stream(dev)
+    sh = stream.cuda_stream
+    elems = sum(math.prod(s) for s in shapes)
+    step_bytes = 2 * 4 * elems * 8
+
+    def step():
+        fftu.fftu_batch_exec(bf, px, py, sh)
+        fftu.fftu_batch_exec(bi, py, pz, sh)
+
+    def per_plan_step():
+        for q, a, b in zip(fwd, px, py):
+            fftu.fftu_exec(q.handle, a, b, sh)
+        for q, a, b in zip(inv, py, pz):
+            fftu.fftu_exec(q.handle, a, b, sh)
+
+    def timed(fn, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(k):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / k
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    if sampler:
+        sampler.start()
+    ms = timed(step, args.steps)
+    clocks = sampler.stop() if sampler else None
+    ms = max_over_ranks(ms, dev)
+    fftu.fftu_batch_check_status(bf)
+    fftu.fftu_batch_check_status(bi)
+    rt = max(float((torch.linalg.vector_norm(z - x) / torch.linalg.vector_norm(x)).item()) for x, z in zip(xs, zs))
+    ms_loop = timed(per_plan_step, max(1, args.steps // 4))
+    launches_loop = sum(q.info["launches_phase_a"] + q.info["launches_phase_b"] for q in fwd + inv)
+
+    e2e = None
+    if not args.no_e2e:
+        outs = [torch.empty_like(h).pin_memory() for h in hosts]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for i in range(2 + args.e2e_steps):
+                if i == 2:
+                    torch.cuda.synchronize(dev)
+                    e0.record(stream)
+                for h, x in zip(hosts, xs):
+                    x.copy_(h, non_blocking=True)
+                step()
+                for o, z in zip(outs, zs):
+                    o.copy_(z, non_blocking=True)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.e2e_steps, dev)
+        e2e = {"value": whole_job_value(step_bytes, e2e_ms, world), "unit": "GB/s",
+               "h2d_bytes_per_step": elems * 8, "d2h_bytes_per_step": elems * 8, "ms_per_step": e2e_ms,
+               "includes": "pinned H2D of every input, batched forward and inverse, D2H of every result"}
+
+    if rank == 0:
+        peak, peak_kind = measured_peak()
+        achieved = step_bytes / 2 / (ms / 2 * 1e-3) / 1e9
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            t0 = time.perf_counter()
+            import oracle
+            sample = shapes[:8]
+            for i, s in enumerate(sample):
+                x = complex_uniform(args.seed + i, s, dtype=np.complex64).astype(np.complex128)
+                oracle.fftn(oracle.fftn(x), inverse=True)
+            t_cpu = time.perf_counter() - t0
+            b_cpu = sum(2 * 4 * math.prod(s) * 8 for s in sample)
+            cpu = {"value": b_cpu / t_cpu / 1e9, "unit": "GB/s", "cores": oracle.max_threads(), "kind": "oracle",
+                   "sample": "FP64 oracle forward+inverse of the first 8 arrays of the batch, GB/s scaled by "
+                             "4*N*8 bytes per transform"}
+        line = {
+            "metric": "batched uneven 3D FFT algorithmic GB/s", "metric_detail": METRIC_DETAIL,
+            "value": whole_job_value(step_bytes, ms, world), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch of {args.batch} uneven complex64 3D transforms (n_l in 32, 64, 128), "
+                                   f"forward+inverse, one persistent launch per direction",
+                       "elements": elems, "bytes_per_array_set": elems * 8,
+                       "l2": "arrays total more than L2 but part of a step's working set stays L2-resident",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "batch_kernel",
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "per_plan_loop": {"ms_per_step": ms_loop, "gpu_launches_per_step": launches_loop,
+                              "value": whole_job_value(step_bytes, ms_loop, world)},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clocks,
+            "round_trip_rel_l2": rt,
+        }
+        print(json.dumps(line), flush=True)
+    fftu.fftu_batch_destroy(bf)
+    fftu.fftu_batch_destroy(bi)
+    for q in fwd + inv:
+        q.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.batch > 0:
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -76,7 +76,8 @@ typedef enum { FFTU_SCHED_AUTO = 0, FFTU_SCHED_GENERIC = 1, FFTU_SCHED_FUSED = 2
 
 typedef struct {
     int schedule;        /* fftu_schedule */
-    int reserved[7];     /* must be zero */
+    int tune;            /* with p == NULL: time candidate grids at plan time and keep the fastest */
+    int reserved[6];     /* must be zero */
 } fftu_options;
 
 typedef struct {
@@ -92,6 +93,8 @@ typedef struct {
     int64_t alg_bytes;         /* algorithmic HBM bytes per transform: 4 * N * sizeof(element) */
     int64_t table_bytes;       /* device bytes of twiddle tables owned by the plan */
     int64_t workspace_bytes;   /* device bytes of workspace owned by the plan */
+    int tuned;                 /* 1 when p was chosen by measurement (fftu_options.tune) */
+    int reserved_info;
 } fftu_info;
 
 /*
@@ -113,7 +116,11 @@ typedef struct {
 fftu_status fftu_plan(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,
                       fftu_handle *out);
 
-/* fftu_plan with options (opts may be NULL = defaults). */
+/* fftu_plan with options (opts may be NULL = defaults).  With p == NULL and opts->tune != 0 the
+ * planner times every candidate grid p_l = min(q, pmax_l), q = 1, 2, 4, ... (pmax_l: the largest power
+ * of two with p_l^2 | n_l), on scratch buffers it allocates for the duration (2 N elements), and keeps
+ * the fastest; the choice is remembered per (shape, dtype, direction, schedule, GPU) in the process's
+ * wisdom table (fftu_wisdom_*).  If the scratch cannot be allocated, the default grid is used. */
 fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,
                          const fftu_options *opts, fftu_handle *out);
 
@@ -213,6 +220,12 @@ fftu_status fftu_batch_create(int count, const fftu_handle *plans, fftu_batch *o
 fftu_status fftu_batch_exec(fftu_batch batch, const void *const *ins, void *const *outs, void *stream);
 fftu_status fftu_batch_check_status(fftu_batch batch);
 fftu_status fftu_batch_destroy(fftu_batch batch);
+
+/* Wisdom: the tuned grids as text lines "fftu-wisdom-v1 <key> <p_1,...,p_d>".  Export writes the
+ * process's table, import merges a file into it, forget clears it. */
+fftu_status fftu_wisdom_export(const char *path);
+fftu_status fftu_wisdom_import(const char *path);
+fftu_status fftu_wisdom_forget(void);
 
 /* Static string for a status code. */
 const char *fftu_status_string(fftu_status s);

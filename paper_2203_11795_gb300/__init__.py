@@ -30,8 +30,8 @@ STATUS_NAMES = {0: "FFTU_OK", 1: "FFTU_ERR_ARG", 2: "FFTU_ERR_DIVISIBILITY", 3: 
 EXPORTS = ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_exec_pointwise", "fftu_destroy",
            "fftu_plan_info",
            "fftu_check_device_status", "fftu_exec_noalloc", "fftu_batch_create", "fftu_batch_exec",
-           "fftu_batch_check_status", "fftu_batch_destroy", "fftu_status_string", "fftu_last_error",
-           "fftu_version")
+           "fftu_batch_check_status", "fftu_batch_destroy", "fftu_wisdom_export", "fftu_wisdom_import",
+           "fftu_wisdom_forget", "fftu_status_string", "fftu_last_error", "fftu_version")
 
 
 class FFTUError(RuntimeError):
@@ -42,7 +42,7 @@ class FFTUError(RuntimeError):
 
 
 class fftu_options(ctypes.Structure):
-    _fields_ = [("schedule", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+    _fields_ = [("schedule", ctypes.c_int), ("tune", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class fftu_info(ctypes.Structure):
@@ -50,7 +50,7 @@ class fftu_info(ctypes.Structure):
                 ("dtype", ctypes.c_int), ("dir", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("launches_phase_a", ctypes.c_int), ("launches_phase_b", ctypes.c_int),
                 ("N", ctypes.c_int64), ("alg_bytes", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
-                ("workspace_bytes", ctypes.c_int64)]
+                ("workspace_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("reserved_info", ctypes.c_int)]
 
 
 def _load_library() -> ctypes.CDLL:
@@ -75,13 +75,17 @@ def _load_library() -> ctypes.CDLL:
     lib.fftu_batch_exec.argtypes = [h, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     lib.fftu_batch_check_status.argtypes = [h]
     lib.fftu_batch_destroy.argtypes = [h]
+    lib.fftu_wisdom_export.argtypes = [ctypes.c_char_p]
+    lib.fftu_wisdom_import.argtypes = [ctypes.c_char_p]
+    lib.fftu_wisdom_forget.argtypes = []
     lib.fftu_status_string.argtypes = [ctypes.c_int]
     lib.fftu_status_string.restype = ctypes.c_char_p
     lib.fftu_last_error.restype = ctypes.c_char_p
     lib.fftu_version.restype = ctypes.c_char_p
     for name in ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_exec_pointwise", "fftu_destroy",
                  "fftu_plan_info", "fftu_check_device_status", "fftu_exec_noalloc", "fftu_batch_create",
-                 "fftu_batch_exec", "fftu_batch_check_status", "fftu_batch_destroy"):
+                 "fftu_batch_exec", "fftu_batch_check_status", "fftu_batch_destroy", "fftu_wisdom_export",
+                 "fftu_wisdom_import", "fftu_wisdom_forget"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -121,9 +125,10 @@ def fftu_plan(d: int, n, p, dtype: int, direction: int) -> int:
     return h.value
 
 
-def fftu_plan_ex(d: int, n, p, dtype: int, direction: int, schedule: int = FFTU_SCHED_AUTO) -> int:
+def fftu_plan_ex(d: int, n, p, dtype: int, direction: int, schedule: int = FFTU_SCHED_AUTO,
+                 tune: bool = False) -> int:
     h = ctypes.c_void_p()
-    opts = fftu_options(schedule=int(schedule))
+    opts = fftu_options(schedule=int(schedule), tune=int(bool(tune)))
     _check(_lib.fftu_plan_ex(int(d), _i64(n), _i64(p), int(dtype), int(direction), ctypes.byref(opts),
                              ctypes.byref(h)), "fftu_plan_ex")
     return h.value
@@ -154,7 +159,7 @@ def fftu_plan_info(plan: int) -> dict:
     return {"d": d, "n": list(info.n[:d]), "p": list(info.p[:d]), "dtype": info.dtype, "dir": info.dir,
             "schedule": info.schedule, "launches_phase_a": info.launches_phase_a,
             "launches_phase_b": info.launches_phase_b, "N": info.N, "alg_bytes": info.alg_bytes,
-            "table_bytes": info.table_bytes, "workspace_bytes": info.workspace_bytes}
+            "table_bytes": info.table_bytes, "workspace_bytes": info.workspace_bytes, "tuned": info.tuned}
 
 
 def fftu_check_device_status(plan: int) -> None:
@@ -189,6 +194,18 @@ def fftu_batch_destroy(batch: int) -> None:
     _check(_lib.fftu_batch_destroy(batch), "fftu_batch_destroy")
 
 
+def fftu_wisdom_export(path: str) -> None:
+    _check(_lib.fftu_wisdom_export(path.encode()), "fftu_wisdom_export")
+
+
+def fftu_wisdom_import(path: str) -> None:
+    _check(_lib.fftu_wisdom_import(path.encode()), "fftu_wisdom_import")
+
+
+def fftu_wisdom_forget() -> None:
+    _check(_lib.fftu_wisdom_forget(), "fftu_wisdom_forget")
+
+
 def fftu_status_string(status: int) -> str:
     return _lib.fftu_status_string(int(status)).decode()
 
@@ -215,14 +232,15 @@ def _dtype_code(torch_dtype) -> int:
 class Plan:
     """A plan for one shape, cyclic grid p, dtype and direction (fftu_plan)."""
 
-    def __init__(self, n, p=None, dtype=None, inverse: bool = False, schedule: int = FFTU_SCHED_AUTO):
+    def __init__(self, n, p=None, dtype=None, inverse: bool = False, schedule: int = FFTU_SCHED_AUTO,
+                 tune: bool = False):
         import torch
         self.n = tuple(int(v) for v in n)
         self.dtype = dtype if dtype is not None else torch.complex64
         code = _dtype_code(self.dtype)
         self.inverse = bool(inverse)
         self.handle = fftu_plan_ex(len(self.n), self.n, None if p is None else list(p), code,
-                                   FFTU_INVERSE if inverse else FFTU_FORWARD, schedule)
+                                   FFTU_INVERSE if inverse else FFTU_FORWARD, schedule, tune)
         self.info = fftu_plan_info(self.handle)
         self.p = tuple(self.info["p"])
 

@@ -102,6 +102,7 @@ struct Plan {
     void *workspace = nullptr;
     size_t workspace_bytes = 0;
     int *dstatus = nullptr;
+    int tuned = 0;
     std::vector<Step> phase_a, phase_b;
     std::vector<Step> phase_a_inplace;  // used when in == out and phase_a cannot run in place
     bool generic_pingpong = false;      // generic phase A alternates between out and the workspace
@@ -519,6 +520,15 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
             set_err("n[%d] = %lld is not a power of two (GPU build supports powers of two)", l, (long long)n[l]);
             return FFTU_ERR_UNSUPPORTED;
         }
+    int tuned = 0;
+    if (!p && opts && opts->tune) {
+        int64_t tp[FFTU_MAX_DIMS];
+        if (autotune_grid(d, n, dtype, dir, sched, tp)) {
+            for (int l = 0; l < d; ++l) pp[l] = tp[l];
+            tuned = 1;
+        }
+        g_err[0] = '\0';
+    }
 
     Plan *pl = new (std::nothrow) Plan();
     if (!pl) {
@@ -532,6 +542,7 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
     }
     pl->dtype = dtype;
     pl->dir = dir;
+    pl->tuned = tuned;
     pl->N = N;
     pl->esize = dtype == FFTU_C128 ? 16 : 8;
     cudaError_t e = cudaGetDevice(&pl->device);
@@ -761,6 +772,7 @@ fftu_status fftu_plan_info(fftu_handle h, fftu_info *info) {
     info->alg_bytes = 4 * pl->N * (int64_t)pl->esize;
     info->table_bytes = (int64_t)pl->table_bytes;
     info->workspace_bytes = (int64_t)pl->workspace_bytes;
+    info->tuned = pl->tuned;
     return FFTU_OK;
 }
 

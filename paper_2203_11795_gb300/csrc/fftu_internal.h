@@ -103,6 +103,9 @@ struct PlanView {
 };
 fftu_status plan_view(fftu_handle h, PlanView *v);
 
+// Plan-time tuning of p (tuner.cu); false: use the default grid.
+bool autotune_grid(int d, const int64_t *n, fftu_dtype dtype, fftu_dir dir, int sched, int64_t *p_out);
+
 // Set the calling thread's detail string returned by fftu_last_error().
 void record_error(const char *msg);
 

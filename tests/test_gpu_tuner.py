@@ -1,0 +1,72 @@
+"""Plan-time tuning of the cyclic grid (fftu_options.tune): the chosen grid is a valid
+Algorithm 2.3 grid, the tuned plan matches the FP64 oracle, and wisdom is recorded and obeyed."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from fftu_inputs import complex_uniform
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fftu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_11795_gb300 import _build
+    _build.build()
+    import paper_2203_11795_gb300 as f
+    return f
+
+
+def _key(shape, dtype_code, direction):
+    import torch
+    name = torch.cuda.get_device_name(0).replace(" ", "_")
+    return f"{len(shape)}:{','.join(str(v) for v in shape)}:{dtype_code}:{direction}:0:{name}"
+
+
+@pytest.mark.parametrize("shape,inverse", [((64, 64, 64), False), ((128, 32), True), ((16, 16, 16, 16), False)])
+def test_tuned_plan_is_valid_and_correct(fftu, tmp_path, shape, inverse):
+    import torch
+    fftu.fftu_wisdom_forget()
+    x = complex_uniform(7, shape, dtype=np.complex64)
+    t = torch.from_numpy(x).cuda()
+    with fftu.Plan(shape, None, dtype=t.dtype, inverse=inverse, tune=True) as plan:
+        info = plan.info
+        assert info["tuned"] == 1
+        for n_l, p_l in zip(shape, info["p"]):
+            assert p_l >= 1 and (p_l & (p_l - 1)) == 0 and n_l % (p_l * p_l) == 0
+        out = plan.exec(t)
+        torch.cuda.synchronize()
+        plan.check_device_status()
+    ref = oracle.fftn(x.astype(np.complex128), inverse=inverse)
+    assert oracle.rel_l2(out.cpu().numpy(), ref) < 1e-5 * math.log2(x.size)
+    path = tmp_path / "w.txt"
+    fftu.fftu_wisdom_export(str(path))
+    code = fftu.FFTU_C64
+    direction = fftu.FFTU_INVERSE if inverse else fftu.FFTU_FORWARD
+    line = f"fftu-wisdom-v1 {_key(shape, code, direction)} {','.join(str(v) for v in info['p'])}"
+    assert line in path.read_text().splitlines()
+
+
+def test_imported_wisdom_is_obeyed(fftu, tmp_path):
+    import torch
+    shape = (32, 32, 32)
+    path = tmp_path / "w.txt"
+    path.write_text(f"fftu-wisdom-v1 {_key(shape, fftu.FFTU_C64, fftu.FFTU_FORWARD)} 2,1,4\n")
+    fftu.fftu_wisdom_forget()
+    fftu.fftu_wisdom_import(str(path))
+    x = complex_uniform(8, shape, dtype=np.complex64)
+    t = torch.from_numpy(x).cuda()
+    with fftu.Plan(shape, None, dtype=t.dtype, tune=True) as plan:
+        assert plan.info["p"] == [2, 1, 4] and plan.info["tuned"] == 1
+        out = plan.exec(t)
+        torch.cuda.synchronize()
+    assert oracle.rel_l2(out.cpu().numpy(), oracle.fftn(x.astype(np.complex128))) < 1e-4
+    # an untuned plan ignores wisdom and keeps the default grid
+    with fftu.Plan(shape, None, dtype=t.dtype) as plan:
+        assert plan.info["tuned"] == 0
+    fftu.fftu_wisdom_forget()
