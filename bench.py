@@ -358,6 +358,9 @@ def run_ours(args):
             "round_trip_rel_l2": rt_err,
         }
         print(json.dumps(line), flush=True)
+        if not rt_err < 1e-3:
+            print(f"round trip relative L2 error {rt_err:.3g}: the timed transforms are wrong", file=sys.stderr)
+            sys.exit(1)
     fwd.close()
     inv.close()
     if world > 1:
@@ -496,6 +499,9 @@ def run_batch(args):
             "round_trip_rel_l2": rt,
         }
         print(json.dumps(line), flush=True)
+        if not rt < 1e-3:
+            print(f"round trip relative L2 error {rt:.3g}: the timed transforms are wrong", file=sys.stderr)
+            sys.exit(1)
     fftu.fftu_batch_destroy(bf)
     fftu.fftu_batch_destroy(bi)
     for q in fwd + inv:

@@ -147,6 +147,7 @@ fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPa
         Gt = a.G;
     } else {  // long line: a tile takes Gt of the G classes (runs of Gt along the line, or V across it)
         V = a.contiguous ? 1 : (inner < (is_double ? 4 : 8) ? inner : (is_double ? 4 : 8));
+        while (V > 1 && a.len * V > maxtile) V /= 2;  // one sub-FFT of every vector must fit the tile
         Gt = maxtile / (a.len * V);
         if (Gt < 1) Gt = 1;
         if (Gt > a.G) Gt = a.G;
@@ -165,6 +166,10 @@ fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPa
     a.lg_chunks = ilog2(chunks);
     a.lg_tpo = a.contiguous ? 0 : ilog2(inner / V);
     const int ept = is_double ? kEptMax / 2 : kEptMax;
+    if (a.tile > 512 * ept) {  // a block of at most 512 threads holds ept values per thread and stage
+        set_err("axis %d: tile of %d elements exceeds 512 threads x %d", l, a.tile, ept);
+        return FFTU_ERR_UNSUPPORTED;
+    }
     int th = (a.tile + ept - 1) / ept;
     th = ((th + 31) / 32) * 32;
     if (th < 32) th = 32;

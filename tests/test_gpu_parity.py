@@ -181,7 +181,11 @@ def test_full_size_512_forward_inverse(fftu, shape, p):
 
 @pytest.mark.parametrize("case", [((32768,), (128,), np.complex64),
                                   ((16384, 16), (128, 4), np.complex64),
-                                  ((8, 8192), (2, 64), np.complex128)], ids=_id)
+                                  ((8, 8192), (2, 64), np.complex128),
+                                  # sub-FFT length x vectors above the tile: fewer vectors per tile
+                                  ((16384, 64), (8, 4), np.complex64),
+                                  ((8192, 32), (4, 2), np.complex128),
+                                  ((32768,), (8,), np.complex64)], ids=_id)
 @pytest.mark.parametrize("inverse", [False, True])
 def test_long_lines(fftu, case, inverse):
     shape, p, dt = case
@@ -191,9 +195,10 @@ def test_long_lines(fftu, case, inverse):
     assert oracle.rel_l2(y, oracle.fftn(x.astype(np.complex128), inverse=inverse)) <= tolerance(dt, x.size)
 
 
-def test_full_size_2d_16384(fftu):
-    """The 2D 16384 x 16384 complex64 workload (p = 128 x 128) against the full FP64 oracle."""
-    shape, p = (16384, 16384), (128, 128)
+@pytest.mark.parametrize("p", [(128, 128), (8, 8)], ids=["p128", "p8"])
+def test_full_size_2d_16384(fftu, p):
+    """The 2D 16384 x 16384 complex64 workload against the full FP64 oracle."""
+    shape = (16384, 16384)
     x = complex_uniform(2025, shape, dtype=np.complex64)
     y, _ = run_gpu(fftu, x, p)
     ref = oracle.fftn(x.astype(np.complex128))
