@@ -31,7 +31,10 @@ EXPORTS = ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_ex
            "fftu_plan_info",
            "fftu_check_device_status", "fftu_exec_noalloc", "fftu_batch_create", "fftu_batch_exec",
            "fftu_batch_check_status", "fftu_batch_destroy", "fftu_wisdom_export", "fftu_wisdom_import",
-           "fftu_wisdom_forget", "fftu_status_string", "fftu_last_error", "fftu_version")
+           "fftu_wisdom_forget", "fftu_status_string", "fftu_last_error", "fftu_version",
+           # include/fftu_serve.h
+           "fftu_server_create", "fftu_server_submit", "fftu_server_poll", "fftu_server_drain",
+           "fftu_server_stats_get", "fftu_server_destroy")
 
 
 class FFTUError(RuntimeError):
@@ -51,6 +54,29 @@ class fftu_info(ctypes.Structure):
                 ("launches_phase_a", ctypes.c_int), ("launches_phase_b", ctypes.c_int),
                 ("N", ctypes.c_int64), ("alg_bytes", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("reserved_info", ctypes.c_int)]
+
+
+class fftu_server_config(ctypes.Structure):
+    _fields_ = [("device_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int), ("streams", ctypes.c_int),
+                ("large_elems", ctypes.c_int64), ("use_graphs", ctypes.c_int), ("max_inflight", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+class fftu_request(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("n", ctypes.c_int64 * FFTU_MAX_DIMS), ("dtype", ctypes.c_int),
+                ("dir", ctypes.c_int), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("tag", ctypes.c_uint64)]
+
+
+class fftu_completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int), ("batch_size", ctypes.c_int),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
+class fftu_server_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "submitted", "completed", "rejected", "batches", "graph_replays", "graph_builds", "direct_launches",
+        "kernel_launches", "instances", "plans", "bytes_in_use", "peak_bytes", "budget_bytes", "evictions",
+        "bytes_h2d", "bytes_d2h")]
 
 
 def _load_library() -> ctypes.CDLL:
@@ -78,6 +104,12 @@ def _load_library() -> ctypes.CDLL:
     lib.fftu_wisdom_export.argtypes = [ctypes.c_char_p]
     lib.fftu_wisdom_import.argtypes = [ctypes.c_char_p]
     lib.fftu_wisdom_forget.argtypes = []
+    lib.fftu_server_create.argtypes = [ctypes.POINTER(fftu_server_config), ctypes.POINTER(h)]
+    lib.fftu_server_submit.argtypes = [h, ctypes.POINTER(fftu_request)]
+    lib.fftu_server_poll.argtypes = [h, ctypes.POINTER(fftu_completion), ctypes.c_int]
+    lib.fftu_server_drain.argtypes = [h, ctypes.c_double]
+    lib.fftu_server_stats_get.argtypes = [h, ctypes.POINTER(fftu_server_stats)]
+    lib.fftu_server_destroy.argtypes = [h]
     lib.fftu_status_string.argtypes = [ctypes.c_int]
     lib.fftu_status_string.restype = ctypes.c_char_p
     lib.fftu_last_error.restype = ctypes.c_char_p
@@ -85,7 +117,8 @@ def _load_library() -> ctypes.CDLL:
     for name in ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_exec_pointwise", "fftu_destroy",
                  "fftu_plan_info", "fftu_check_device_status", "fftu_exec_noalloc", "fftu_batch_create",
                  "fftu_batch_exec", "fftu_batch_check_status", "fftu_batch_destroy", "fftu_wisdom_export",
-                 "fftu_wisdom_import", "fftu_wisdom_forget"):
+                 "fftu_wisdom_import", "fftu_wisdom_forget", "fftu_server_create", "fftu_server_submit",
+                 "fftu_server_poll", "fftu_server_drain", "fftu_server_stats_get", "fftu_server_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -204,6 +237,47 @@ def fftu_wisdom_import(path: str) -> None:
 
 def fftu_wisdom_forget() -> None:
     _check(_lib.fftu_wisdom_forget(), "fftu_wisdom_forget")
+
+
+def fftu_server_create(device_bytes: int = 0, max_batch: int = 0, streams: int = 0, large_elems: int = 0,
+                       use_graphs: bool = True, max_inflight: int = 0) -> int:
+    cfg = fftu_server_config(device_bytes=int(device_bytes), max_batch=int(max_batch), streams=int(streams),
+                             large_elems=int(large_elems), use_graphs=int(bool(use_graphs)),
+                             max_inflight=int(max_inflight))
+    h = ctypes.c_void_p()
+    _check(_lib.fftu_server_create(ctypes.byref(cfg), ctypes.byref(h)), "fftu_server_create")
+    return h.value
+
+
+def fftu_server_submit(server: int, n, dtype: int, direction: int, in_ptr: int, out_ptr: int, tag: int) -> None:
+    n = [int(v) for v in n]
+    r = fftu_request(d=len(n), dtype=int(dtype), dir=int(direction), in_=in_ptr, out=out_ptr, tag=int(tag))
+    for i, v in enumerate(n):
+        r.n[i] = v
+    _check(_lib.fftu_server_submit(server, ctypes.byref(r)), "fftu_server_submit")
+
+
+def fftu_server_poll(server: int, max_items: int = 1024) -> list:
+    buf = (fftu_completion * max_items)()
+    k = _lib.fftu_server_poll(server, buf, max_items)
+    if k < 0:
+        raise FFTUError(1, "fftu_server_poll")
+    return [{"tag": c.tag, "status": c.status, "batch_size": c.batch_size, "submit_s": c.submit_s,
+             "start_s": c.start_s, "done_s": c.done_s} for c in buf[:k]]
+
+
+def fftu_server_drain(server: int, timeout_s: float = 60.0) -> None:
+    _check(_lib.fftu_server_drain(server, float(timeout_s)), "fftu_server_drain")
+
+
+def fftu_server_stats_get(server: int) -> dict:
+    st = fftu_server_stats()
+    _check(_lib.fftu_server_stats_get(server, ctypes.byref(st)), "fftu_server_stats_get")
+    return {name: getattr(st, name) for name, _ in fftu_server_stats._fields_}
+
+
+def fftu_server_destroy(server: int) -> None:
+    _check(_lib.fftu_server_destroy(server), "fftu_server_destroy")
 
 
 def fftu_status_string(status: int) -> str:

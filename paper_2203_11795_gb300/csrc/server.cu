@@ -1,0 +1,694 @@
+// Serving loop over whole transforms (fftu_serve.h): per-key queues, memory-budget admission,
+// same-key batching into one persistent launch, CUDA graph replay, completion polling.
+//
+// Data structures
+//   Key       (d, n, dtype, dir): one resident plan (twiddle tables) shared by every batch of the key.
+//   Instance  a resident launch of k requests of one key: device slots for k inputs and k outputs,
+//             its own fftu_batch (the batch's counters are per launch, so an instance runs one
+//             launch at a time) or, for large requests, its own plan (a plan's workspace is per
+//             launch too), a stream, a completion event and, once used with page-locked buffers,
+//             an instantiated graph whose copy nodes are re-pointed at each replay.
+// The server thread alone touches keys and instances; submitters and pollers share two
+// mutex-protected queues with it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "fftu.h"
+#include "fftu_serve.h"
+
+namespace fftu {
+void record_error(const char *msg);
+}
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Key {
+    int d = 0;
+    int64_t n[FFTU_MAX_DIMS] = {};
+    int dtype = 0, dir = 0;
+    bool operator<(const Key &o) const {
+        if (d != o.d) return d < o.d;
+        if (dtype != o.dtype) return dtype < o.dtype;
+        if (dir != o.dir) return dir < o.dir;
+        for (int l = 0; l < d; ++l)
+            if (n[l] != o.n[l]) return n[l] < o.n[l];
+        return false;
+    }
+};
+
+struct Req {
+    fftu_request r;
+    double t_submit = 0;
+};
+
+struct KeyState;
+
+struct Instance {
+    KeyState *ks = nullptr;
+    int k = 0;
+    bool large = false;
+    void *dev = nullptr;  // [k inputs][k outputs]
+    size_t slot_bytes = 0;
+    size_t bytes = 0;     // device bytes charged to the budget
+    fftu_batch batch = nullptr;
+    fftu_handle own_plan = nullptr;
+    int launches = 0;     // kernels per use
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<cudaGraphNode_t> h2d, d2h;
+    bool graph_failed = false;
+    bool busy = false;
+    std::vector<Req> reqs;
+    double t_start = 0;
+    uint64_t last_used = 0;
+
+    void *in_slot(int i) const { return static_cast<char *>(dev) + (size_t)i * slot_bytes; }
+    void *out_slot(int i) const { return static_cast<char *>(dev) + (size_t)(k + i) * slot_bytes; }
+};
+
+struct KeyState {
+    Key key;
+    int64_t N = 0;
+    size_t esize = 0;
+    fftu_handle plan = nullptr;  // shared by the batched instances
+    size_t plan_bytes = 0;
+    bool solo = false;           // requests run alone through their own plan (large, or not batchable)
+    std::deque<Req> pending;
+    std::vector<std::unique_ptr<Instance>> inst;
+    uint64_t last_used = 0;
+};
+
+}  // namespace
+
+struct fftu_server_st {
+    fftu_server_config cfg;
+    int device = 0;
+    Clock::time_point t0;
+    std::vector<cudaStream_t> streams;
+    int next_stream = 0;
+
+    std::mutex in_mu;              // inbox and counters shared with submitters
+    std::condition_variable in_cv;
+    std::deque<Req> inbox;
+    std::mutex out_mu;             // completions shared with pollers
+    std::deque<fftu_completion> outbox;
+    std::atomic<int64_t> outstanding{0};
+    std::atomic<bool> stop{false};
+
+    std::mutex stats_mu;
+    fftu_server_stats stats;
+
+    std::map<Key, std::unique_ptr<KeyState>> keys;  // server thread only
+    size_t used = 0;
+    uint64_t tick = 0;
+    std::thread thread;
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+namespace {
+
+int64_t elems(const Key &k) {
+    int64_t N = 1;
+    for (int l = 0; l < k.d; ++l) N *= k.n[l];
+    return N;
+}
+
+void complete(fftu_server_st *S, const Req &q, int status, int batch_size, double t_start) {
+    fftu_completion c;
+    c.tag = q.r.tag;
+    c.status = status;
+    c.batch_size = batch_size;
+    c.submit_s = q.t_submit;
+    c.start_s = t_start;
+    c.done_s = S->now();
+    {
+        std::lock_guard<std::mutex> lk(S->out_mu);
+        S->outbox.push_back(c);
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->stats_mu);
+        S->stats.completed++;
+        if (status != FFTU_OK && batch_size == 0) S->stats.rejected++;
+    }
+    S->outstanding.fetch_sub(1);
+}
+
+void update_bytes(fftu_server_st *S) {
+    std::lock_guard<std::mutex> lk(S->stats_mu);
+    S->stats.bytes_in_use = (int64_t)S->used;
+    S->stats.peak_bytes = std::max(S->stats.peak_bytes, (int64_t)S->used);
+    int64_t ni = 0, np = 0;
+    for (auto &kv : S->keys) {
+        ni += (int64_t)kv.second->inst.size();
+        np += kv.second->plan ? 1 : 0;
+        for (auto &in : kv.second->inst) np += in->own_plan ? 1 : 0;
+    }
+    S->stats.instances = ni;
+    S->stats.plans = np;
+}
+
+size_t plan_device_bytes(fftu_handle h) {
+    fftu_info info;
+    if (fftu_plan_info(h, &info) != FFTU_OK) return 0;
+    return (size_t)(info.table_bytes + info.workspace_bytes) + 256;
+}
+
+int plan_launches(fftu_handle h) {
+    fftu_info info;
+    if (fftu_plan_info(h, &info) != FFTU_OK) return 0;
+    return info.launches_phase_a + info.launches_phase_b;
+}
+
+void destroy_instance(fftu_server_st *S, Instance *in) {
+    if (in->gexec) cudaGraphExecDestroy(in->gexec);
+    if (in->graph) cudaGraphDestroy(in->graph);
+    if (in->batch) fftu_batch_destroy(in->batch);
+    if (in->own_plan) fftu_destroy(in->own_plan);
+    if (in->done) cudaEventDestroy(in->done);
+    if (in->dev) cudaFree(in->dev);
+    S->used -= in->bytes;
+}
+
+// Free idle instances and unused plans, least recently used first, until `need` more bytes fit.
+bool make_room(fftu_server_st *S, size_t need, const KeyState *keep) {
+    const size_t budget = (size_t)S->cfg.device_bytes;
+    while (S->used + need > budget) {
+        Instance *victim = nullptr;
+        KeyState *vks = nullptr;
+        KeyState *plan_victim = nullptr;
+        for (auto &kv : S->keys) {
+            KeyState *ks = kv.second.get();
+            for (auto &in : ks->inst)
+                if (!in->busy && (!victim || in->last_used < victim->last_used)) {
+                    victim = in.get();
+                    vks = ks;
+                }
+            if (ks != keep && ks->plan && ks->inst.empty() && ks->pending.empty() &&
+                (!plan_victim || ks->last_used < plan_victim->last_used))
+                plan_victim = ks;
+        }
+        if (victim) {
+            destroy_instance(S, victim);
+            auto &v = vks->inst;
+            v.erase(std::remove_if(v.begin(), v.end(), [&](const std::unique_ptr<Instance> &p) { return p.get() == victim; }),
+                    v.end());
+        } else if (plan_victim) {
+            fftu_destroy(plan_victim->plan);
+            plan_victim->plan = nullptr;
+            S->used -= plan_victim->plan_bytes;
+            plan_victim->plan_bytes = 0;
+        } else {
+            return false;
+        }
+        std::lock_guard<std::mutex> lk(S->stats_mu);
+        S->stats.evictions++;
+    }
+    return true;
+}
+
+// The resident plan of a key (batched requests); nullptr if it does not fit now or fails.
+fftu_status ensure_plan(fftu_server_st *S, KeyState *ks) {
+    if (ks->plan) return FFTU_OK;
+    fftu_handle h = nullptr;
+    fftu_status st = fftu_plan(ks->key.d, ks->key.n, nullptr, (fftu_dtype)ks->key.dtype, (fftu_dir)ks->key.dir, &h);
+    if (st != FFTU_OK) return st;
+    const size_t b = plan_device_bytes(h);
+    if (S->used + b > (size_t)S->cfg.device_bytes && !make_room(S, b, ks)) {
+        fftu_destroy(h);
+        return FFTU_ERR_NOMEM;
+    }
+    ks->plan = h;
+    ks->plan_bytes = b;
+    S->used += b;
+    return FFTU_OK;
+}
+
+// A new instance of k requests of ks; nullptr when the budget cannot hold it right now.
+Instance *new_instance(fftu_server_st *S, KeyState *ks, int k, bool large, fftu_status *err) {
+    *err = FFTU_OK;
+    auto in = std::make_unique<Instance>();
+    in->ks = ks;
+    in->k = k;
+    in->large = large;
+    in->slot_bytes = ((size_t)ks->N * ks->esize + 255) / 256 * 256;
+    size_t bytes = 2 * (size_t)k * in->slot_bytes;
+    if (large) {
+        fftu_status st = fftu_plan(ks->key.d, ks->key.n, nullptr, (fftu_dtype)ks->key.dtype, (fftu_dir)ks->key.dir,
+                                   &in->own_plan);
+        if (st != FFTU_OK) {
+            *err = st;
+            return nullptr;
+        }
+        bytes += plan_device_bytes(in->own_plan);
+        in->launches = plan_launches(in->own_plan);
+    } else {
+        fftu_status st = ensure_plan(S, ks);
+        if (st != FFTU_OK) {
+            *err = st == FFTU_ERR_NOMEM ? FFTU_OK : st;  // no room yet: wait
+            return nullptr;
+        }
+        bytes += 4096 * 4;  // the batch's job table and counters
+        in->launches = 1;
+    }
+    if (S->used + bytes > (size_t)S->cfg.device_bytes && !make_room(S, bytes, ks)) {
+        if (in->own_plan) fftu_destroy(in->own_plan);
+        return nullptr;
+    }
+    if (cudaMalloc(&in->dev, 2 * (size_t)k * in->slot_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        if (in->own_plan) fftu_destroy(in->own_plan);
+        return nullptr;
+    }
+    if (!large) {
+        std::vector<fftu_handle> hs(k, ks->plan);
+        fftu_status st = fftu_batch_create(k, hs.data(), &in->batch);
+        if (st != FFTU_OK) {
+            cudaFree(in->dev);
+            if (st == FFTU_ERR_UNSUPPORTED) {
+                ks->solo = true;  // e.g. long lines: phase A alternates with a workspace
+                return nullptr;   // the caller retries as a solo request
+            }
+            *err = st;
+            return nullptr;
+        }
+    }
+    cudaEventCreateWithFlags(&in->done, cudaEventDisableTiming);
+    in->stream = S->streams[S->next_stream];
+    S->next_stream = (S->next_stream + 1) % (int)S->streams.size();
+    in->bytes = bytes;
+    S->used += bytes;
+    Instance *raw = in.get();
+    ks->inst.push_back(std::move(in));
+    return raw;
+}
+
+fftu_status compute(Instance *in, cudaStream_t st) {
+    if (in->large) return fftu_exec(in->own_plan, in->in_slot(0), in->out_slot(0), st);
+    std::vector<const void *> ins(in->k);
+    std::vector<void *> outs(in->k);
+    for (int i = 0; i < in->k; ++i) {
+        ins[i] = in->in_slot(i);
+        outs[i] = in->out_slot(i);
+    }
+    return fftu_batch_exec(in->batch, ins.data(), outs.data(), st);
+}
+
+bool build_graph(Instance *in) {
+    const size_t bytes = (size_t)in->ks->N * in->ks->esize;
+    cudaGraph_t g = nullptr, child = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+    bool ok = true;
+    in->h2d.assign(in->k, nullptr);
+    in->d2h.assign(in->k, nullptr);
+    for (int i = 0; ok && i < in->k; ++i)
+        ok = cudaGraphAddMemcpyNode1D(&in->h2d[i], g, nullptr, 0, in->in_slot(i), in->reqs[i].r.in, bytes,
+                                      cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) {
+        ok = cudaStreamBeginCapture(in->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            const fftu_status st = compute(in, in->stream);
+            ok = cudaStreamEndCapture(in->stream, &child) == cudaSuccess && st == FFTU_OK && child;
+        }
+    }
+    cudaGraphNode_t cn = nullptr;
+    if (ok) ok = cudaGraphAddChildGraphNode(&cn, g, in->h2d.data(), in->k, child) == cudaSuccess;
+    for (int i = 0; ok && i < in->k; ++i)
+        ok = cudaGraphAddMemcpyNode1D(&in->d2h[i], g, &cn, 1, in->reqs[i].r.out, in->out_slot(i), bytes,
+                                      cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (child) cudaGraphDestroy(child);
+    if (ok) ok = cudaGraphInstantiate(&in->gexec, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (in->gexec) cudaGraphExecDestroy(in->gexec);
+        in->gexec = nullptr;
+        cudaGraphDestroy(g);
+        return false;
+    }
+    in->graph = g;
+    return true;
+}
+
+bool page_locked(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// Issue one use of an instance for its reqs; on failure every request completes with the error.
+void launch(fftu_server_st *S, Instance *in) {
+    const size_t bytes = (size_t)in->ks->N * in->ks->esize;
+    in->busy = true;
+    in->t_start = S->now();
+    in->last_used = ++S->tick;
+    in->ks->last_used = S->tick;
+    bool locked = S->cfg.use_graphs && !in->graph_failed;
+    for (int i = 0; locked && i < in->k; ++i) locked = page_locked(in->reqs[i].r.in) && page_locked(in->reqs[i].r.out);
+    fftu_status st = FFTU_OK;
+    bool graphed = false, built = false;
+    if (locked) {
+        if (!in->gexec) {
+            built = build_graph(in);
+            if (!built) in->graph_failed = true;
+        }
+        if (in->gexec) {
+            bool ok = true;
+            for (int i = 0; ok && i < in->k; ++i) {
+                ok = cudaGraphExecMemcpyNodeSetParams1D(in->gexec, in->h2d[i], in->in_slot(i), in->reqs[i].r.in, bytes,
+                                                       cudaMemcpyHostToDevice) == cudaSuccess &&
+                     cudaGraphExecMemcpyNodeSetParams1D(in->gexec, in->d2h[i], in->reqs[i].r.out, in->out_slot(i),
+                                                       bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
+            }
+            if (ok) ok = cudaGraphLaunch(in->gexec, in->stream) == cudaSuccess;
+            if (ok) {
+                graphed = true;
+            } else {
+                cudaGetLastError();
+                in->graph_failed = true;
+            }
+        }
+    }
+    if (!graphed) {
+        for (int i = 0; st == FFTU_OK && i < in->k; ++i)
+            if (cudaMemcpyAsync(in->in_slot(i), in->reqs[i].r.in, bytes, cudaMemcpyHostToDevice, in->stream) !=
+                cudaSuccess)
+                st = FFTU_ERR_CUDA;
+        if (st == FFTU_OK) st = compute(in, in->stream);
+        for (int i = 0; st == FFTU_OK && i < in->k; ++i)
+            if (cudaMemcpyAsync(in->reqs[i].r.out, in->out_slot(i), bytes, cudaMemcpyDeviceToHost, in->stream) !=
+                cudaSuccess)
+                st = FFTU_ERR_CUDA;
+    }
+    if (st == FFTU_OK && cudaEventRecord(in->done, in->stream) != cudaSuccess) st = FFTU_ERR_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(S->stats_mu);
+        S->stats.batches++;
+        S->stats.kernel_launches += in->launches;
+        if (graphed) S->stats.graph_replays++;
+        else S->stats.direct_launches++;
+        if (built) S->stats.graph_builds++;
+        S->stats.bytes_h2d += (int64_t)(bytes * in->k);
+        S->stats.bytes_d2h += (int64_t)(bytes * in->k);
+    }
+    if (st != FFTU_OK) {
+        cudaGetLastError();
+        cudaStreamSynchronize(in->stream);
+        for (auto &q : in->reqs) complete(S, q, st, in->k, in->t_start);
+        in->reqs.clear();
+        in->busy = false;
+    }
+}
+
+// Completed instances: stamp their requests and free the instance for reuse.
+bool reap(fftu_server_st *S) {
+    bool any = false;
+    for (auto &kv : S->keys)
+        for (auto &in : kv.second->inst) {
+            if (!in->busy) continue;
+            const cudaError_t e = cudaEventQuery(in->done);
+            if (e == cudaErrorNotReady) continue;
+            int status = e == cudaSuccess ? FFTU_OK : FFTU_ERR_CUDA;
+            if (e != cudaSuccess) cudaGetLastError();
+            for (auto &q : in->reqs) complete(S, q, status, in->k, in->t_start);
+            in->reqs.clear();
+            in->busy = false;
+            any = true;
+        }
+    return any;
+}
+
+bool any_busy(fftu_server_st *S);
+
+int pow2_floor(int v) {
+    int k = 1;
+    while (2 * k <= v) k *= 2;
+    return k;
+}
+
+// Start batches for every key with queued requests, oldest head first.
+bool dispatch(fftu_server_st *S) {
+    std::vector<KeyState *> order;
+    for (auto &kv : S->keys)
+        if (!kv.second->pending.empty()) order.push_back(kv.second.get());
+    std::sort(order.begin(), order.end(),
+              [](const KeyState *a, const KeyState *b) { return a->pending.front().t_submit < b->pending.front().t_submit; });
+    bool any = false;
+    int inflight = 0;
+    for (auto &kv : S->keys)
+        for (auto &in : kv.second->inst) inflight += in->busy ? 1 : 0;
+    for (KeyState *ks : order) {
+        if (ks->N >= S->cfg.large_elems) ks->solo = true;
+        while (!ks->pending.empty() && inflight < S->cfg.max_inflight) {
+            const bool large = ks->solo;
+            const int k = large ? 1 : pow2_floor(std::min<int>((int)ks->pending.size(), S->cfg.max_batch));
+            Instance *in = nullptr;
+            for (auto &c : ks->inst)
+                if (!c->busy && c->k == k && c->large == large) {
+                    in = c.get();
+                    break;
+                }
+            fftu_status err = FFTU_OK;
+            if (!in) in = new_instance(S, ks, k, large, &err);
+            if (!in && !large && ks->solo) continue;  // not batchable: go again as solo requests
+            if (!in && err == FFTU_ERR_NOMEM && any_busy(S)) err = FFTU_OK;  // wait for memory
+            if (!in) {
+                if (err != FFTU_OK) {  // the key cannot run at all
+                    while (!ks->pending.empty()) {
+                        complete(S, ks->pending.front(), err, 0, 0);
+                        ks->pending.pop_front();
+                    }
+                }
+                break;  // wait for memory
+            }
+            in->reqs.assign(ks->pending.begin(), ks->pending.begin() + k);
+            ks->pending.erase(ks->pending.begin(), ks->pending.begin() + k);
+            launch(S, in);
+            inflight += in->busy ? 1 : 0;
+            any = true;
+        }
+    }
+    update_bytes(S);
+    return any;
+}
+
+void intake(fftu_server_st *S, std::deque<Req> &batch) {
+    for (auto &q : batch) {
+        Key k;
+        k.d = q.r.d;
+        for (int l = 0; l < k.d; ++l) k.n[l] = q.r.n[l];
+        k.dtype = q.r.dtype;
+        k.dir = q.r.dir;
+        auto it = S->keys.find(k);
+        if (it == S->keys.end()) {
+            auto ks = std::make_unique<KeyState>();
+            ks->key = k;
+            ks->N = elems(k);
+            ks->esize = k.dtype == FFTU_C128 ? 16 : 8;
+            it = S->keys.emplace(k, std::move(ks)).first;
+        }
+        KeyState *ks = it->second.get();
+        // a request that cannot fit even alone is refused at once (a plan's workspace is at most
+        // N elements, its twiddle tables sum_l n_l elements)
+        const size_t slot = ((size_t)ks->N * ks->esize + 255) / 256 * 256;
+        const size_t alone = 2 * slot + (ks->plan ? 0 : (size_t)ks->N * ks->esize + (64u << 10));
+        if (alone > (size_t)S->cfg.device_bytes) {
+            complete(S, q, FFTU_ERR_NOMEM, 0, 0);
+            continue;
+        }
+        ks->pending.push_back(q);
+    }
+    batch.clear();
+}
+
+bool any_busy(fftu_server_st *S) {
+    for (auto &kv : S->keys)
+        for (auto &in : kv.second->inst)
+            if (in->busy) return true;
+    return false;
+}
+
+bool any_pending(fftu_server_st *S) {
+    for (auto &kv : S->keys)
+        if (!kv.second->pending.empty()) return true;
+    return false;
+}
+
+void server_main(fftu_server_st *S) {
+    cudaSetDevice(S->device);
+    std::deque<Req> local;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(S->in_mu);
+            if (S->inbox.empty() && !S->stop.load() && !any_busy(S) && !any_pending(S))
+                S->in_cv.wait_for(lk, std::chrono::milliseconds(5));
+            local.swap(S->inbox);
+        }
+        intake(S, local);
+        const bool reaped = reap(S);
+        const bool started = dispatch(S);
+        if (S->stop.load() && !any_busy(S)) break;
+        if (!reaped && !started && (any_busy(S) || any_pending(S)))
+            std::this_thread::sleep_for(std::chrono::microseconds(5));
+    }
+    for (auto &kv : S->keys)
+        for (auto &q : kv.second->pending) complete(S, q, FFTU_ERR_ARG, 0, 0);
+    {
+        std::lock_guard<std::mutex> lk(S->in_mu);
+        for (auto &q : S->inbox) complete(S, q, FFTU_ERR_ARG, 0, 0);
+        S->inbox.clear();
+    }
+    for (auto &kv : S->keys) {
+        for (auto &in : kv.second->inst) destroy_instance(S, in.get());
+        kv.second->inst.clear();
+        if (kv.second->plan) fftu_destroy(kv.second->plan);
+        kv.second->plan = nullptr;
+    }
+    S->keys.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+fftu_status fftu_server_create(const fftu_server_config *cfg, fftu_server *out) {
+    if (!out) return FFTU_ERR_ARG;
+    *out = nullptr;
+    fftu_server_config c;
+    std::memset(&c, 0, sizeof(c));
+    if (cfg) c = *cfg;
+    for (int i = 0; i < 6; ++i)
+        if (c.reserved[i]) {
+            fftu::record_error("server: reserved config fields must be zero");
+            return FFTU_ERR_ARG;
+        }
+    if (c.max_batch == 0) c.max_batch = 64;
+    if (c.streams == 0) c.streams = 4;
+    if (c.large_elems == 0) c.large_elems = 1ll << 22;
+    if (c.max_inflight == 0) c.max_inflight = 2 * c.streams;
+    if (c.max_batch < 1 || c.max_batch > 128 || c.streams < 1 || c.streams > 16 || c.large_elems < 1 ||
+        c.device_bytes < 0 || c.max_inflight < 1 || c.max_inflight > 256) {
+        fftu::record_error("server: max_batch must be in [1, 128], streams in [1, 16], max_inflight in [1, 256], "
+                           "large_elems >= 1");
+        return FFTU_ERR_ARG;
+    }
+    auto S = new (std::nothrow) fftu_server_st();
+    if (!S) return FFTU_ERR_NOMEM;
+    if (cudaGetDevice(&S->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete S;
+        fftu::record_error("server: no CUDA device");
+        return FFTU_ERR_CUDA;
+    }
+    if (c.device_bytes == 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            delete S;
+            return FFTU_ERR_CUDA;
+        }
+        c.device_bytes = (int64_t)(fr / 2);
+    }
+    S->cfg = c;
+    std::memset(&S->stats, 0, sizeof(S->stats));
+    S->stats.budget_bytes = c.device_bytes;
+    S->t0 = Clock::now();
+    for (int i = 0; i < c.streams; ++i) {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto x : S->streams) cudaStreamDestroy(x);
+            delete S;
+            return FFTU_ERR_CUDA;
+        }
+        S->streams.push_back(s);
+    }
+    S->thread = std::thread(server_main, S);
+    *out = S;
+    return FFTU_OK;
+}
+
+fftu_status fftu_server_submit(fftu_server S, const fftu_request *req) {
+    if (!S || !req || !req->in || !req->out) return FFTU_ERR_ARG;
+    if (req->d < 1 || req->d > FFTU_MAX_DIMS || (req->dtype != FFTU_C64 && req->dtype != FFTU_C128) ||
+        (req->dir != FFTU_FORWARD && req->dir != FFTU_INVERSE)) {
+        fftu::record_error("server: bad d, dtype or direction");
+        return FFTU_ERR_ARG;
+    }
+    for (int l = 0; l < req->d; ++l)
+        if (req->n[l] < 1 || (req->n[l] & (req->n[l] - 1))) {
+            fftu::record_error("server: every n_l must be a power of two");
+            return req->n[l] < 1 ? FFTU_ERR_ARG : FFTU_ERR_UNSUPPORTED;
+        }
+    Req q;
+    q.r = *req;
+    q.t_submit = S->now();
+    S->outstanding.fetch_add(1);
+    {
+        std::lock_guard<std::mutex> lk(S->stats_mu);
+        S->stats.submitted++;
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->in_mu);
+        S->inbox.push_back(q);
+    }
+    S->in_cv.notify_one();
+    return FFTU_OK;
+}
+
+int fftu_server_poll(fftu_server S, fftu_completion *out, int max) {
+    if (!S || (!out && max > 0) || max < 0) return -1;
+    std::lock_guard<std::mutex> lk(S->out_mu);
+    int n = 0;
+    while (n < max && !S->outbox.empty()) {
+        out[n++] = S->outbox.front();
+        S->outbox.pop_front();
+    }
+    return n;
+}
+
+fftu_status fftu_server_drain(fftu_server S, double timeout_s) {
+    if (!S) return FFTU_ERR_ARG;
+    const auto end = Clock::now() + std::chrono::duration<double>(timeout_s);
+    while (S->outstanding.load() > 0) {
+        if (Clock::now() > end) return FFTU_ERR_TIMEOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    return FFTU_OK;
+}
+
+fftu_status fftu_server_stats_get(fftu_server S, fftu_server_stats *st) {
+    if (!S || !st) return FFTU_ERR_ARG;
+    std::lock_guard<std::mutex> lk(S->stats_mu);
+    *st = S->stats;
+    return FFTU_OK;
+}
+
+fftu_status fftu_server_destroy(fftu_server S) {
+    if (!S) return FFTU_OK;
+    S->stop.store(true);
+    S->in_cv.notify_one();
+    if (S->thread.joinable()) S->thread.join();
+    for (auto s : S->streams) cudaStreamDestroy(s);
+    delete S;
+    return FFTU_OK;
+}
+
+}  // extern "C"

@@ -1,6 +1,7 @@
 """The C-ABI library loads and exports every symbol include/fftu.h declares,
 and host-side validation rejects bad plans before touching a GPU."""
 import ctypes
+import glob
 import os
 import re
 import subprocess
@@ -9,6 +10,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "fftu.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 @pytest.fixture(scope="module")
@@ -19,7 +21,7 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(fftu_[a-z_]+)\s*\(", text)))
 
@@ -68,3 +70,17 @@ def test_bad_dtype_dir_and_d():
         with pytest.raises(f.FFTUError) as ei:
             f.fftu_plan(*args)
         assert ei.value.status == 1  # FFTU_ERR_ARG
+
+
+def test_server_config_validation():
+    """Invalid server configs are refused before any CUDA call; bad handles are reported."""
+    import paper_2203_11795_gb300 as f
+    for cfg in ({"max_batch": 200}, {"streams": 17}, {"max_batch": -1}, {"max_inflight": 300}):
+        with pytest.raises(f.FFTUError) as ei:
+            f.fftu_server_create(**cfg)
+        assert ei.value.status == 1
+    with pytest.raises(f.FFTUError):
+        f.fftu_server_drain(None, 0.0)
+    with pytest.raises(f.FFTUError):
+        f.fftu_server_poll(None, 4)
+    f.fftu_server_destroy(None)
