@@ -49,6 +49,9 @@ def parse_args():
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=1000.0, help="offered Poisson rate, requests per second")
     ap.add_argument("--serve-warmup", type=int, default=400)
+    ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--serve-inflight", type=int, default=0, help="0 = 2 x streams")
+    ap.add_argument("--serve-piece-mib", type=int, default=0, help="host copies in pieces of this many MiB")
     ap.add_argument("--batch", type=int, default=0,
                     help="K > 0: time K uneven 3D transforms (n_l in {32, 64, 128}) in one persistent launch "
                          "per direction instead of the single-array workload")
@@ -420,7 +423,8 @@ def run_serving(fftu, args, local):
     cv = threading.Condition(lock)
     slot_of, meta = {}, {}
     stalls = [0]
-    server = fftu.fftu_server_create(max_batch=64, streams=4)
+    server = fftu.fftu_server_create(max_batch=64, streams=args.serve_streams, max_inflight=args.serve_inflight,
+                                     copy_piece_mib=args.serve_piece_mib)
 
     def generator():
         t_next = time.perf_counter()
@@ -510,6 +514,8 @@ def run_serving(fftu, args, local):
         "gbs_algorithmic": alg / span / 1e9, "gbs_host_copies": moved / span / 1e9,
         "failed": len(bad), "pool_stalls": stalls[0], "wall_s": wall, "pinned_pool_alloc_s": t_alloc,
         "served_vs_direct_max_rel_l2": worst, **d, "per_class": per_class,
+        "server": {"streams": args.serve_streams, "max_inflight": args.serve_inflight or 2 * args.serve_streams,
+                   "max_batch": 64, "copy_piece_mib": args.serve_piece_mib},
         "mix": "shapes uniform over 32^3, 64^3, 128^3, 256^3, 1024^2, 2048^2, 4096^2; complex128 w.p. 0.1; "
                "forward/inverse equiprobable; Poisson arrivals; latency = server completion - submission",
     }

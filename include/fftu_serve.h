@@ -45,7 +45,9 @@ typedef struct {
     int use_graphs;       /* nonzero: replay captured CUDA graphs for page-locked requests */
     int max_inflight;     /* launches in flight at once, 1..256; 0 = 2 x streams.  Requests that
                              arrive while the limit is reached queue, and join one launch */
-    int reserved[6];      /* must be zero */
+    int copy_piece_mib;   /* > 0: host copies in pieces of this many MiB, one after another, so that
+                             other requests' copies can run between them; 0 = one copy per array */
+    int reserved[5];      /* must be zero */
 } fftu_server_config;
 
 typedef struct {

@@ -59,7 +59,7 @@ class fftu_info(ctypes.Structure):
 class fftu_server_config(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int), ("streams", ctypes.c_int),
                 ("large_elems", ctypes.c_int64), ("use_graphs", ctypes.c_int), ("max_inflight", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("copy_piece_mib", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class fftu_request(ctypes.Structure):
@@ -240,10 +240,10 @@ def fftu_wisdom_forget() -> None:
 
 
 def fftu_server_create(device_bytes: int = 0, max_batch: int = 0, streams: int = 0, large_elems: int = 0,
-                       use_graphs: bool = True, max_inflight: int = 0) -> int:
+                       use_graphs: bool = True, max_inflight: int = 0, copy_piece_mib: int = 0) -> int:
     cfg = fftu_server_config(device_bytes=int(device_bytes), max_batch=int(max_batch), streams=int(streams),
                              large_elems=int(large_elems), use_graphs=int(bool(use_graphs)),
-                             max_inflight=int(max_inflight))
+                             max_inflight=int(max_inflight), copy_piece_mib=int(copy_piece_mib))
     h = ctypes.c_void_p()
     _check(_lib.fftu_server_create(ctypes.byref(cfg), ctypes.byref(h)), "fftu_server_create")
     return h.value

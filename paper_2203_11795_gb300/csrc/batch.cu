@@ -283,9 +283,14 @@ fftu_status batch_create(int count, const fftu_handle *plans, Batch **out_batch)
     b->task_ctr = reinterpret_cast<unsigned long long *>(base + jb + fb);
     b->status = reinterpret_cast<int *>(base + jb + fb + 8);
     b->done = reinterpret_cast<unsigned *>(base + jb + fb + 16);
-    e = cudaMemcpy(b->jobs, jobs.data(), jb, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->firsts, firsts.data(), fb, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(b->status, 0, sizeof(int));
+    // uploads on a private stream: creating a batch does not wait for transforms in flight
+    cudaStream_t ps = nullptr;
+    e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->jobs, jobs.data(), jb, cudaMemcpyHostToDevice, ps);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->firsts, firsts.data(), fb, cudaMemcpyHostToDevice, ps);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, sizeof(int), ps);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
+    if (ps) cudaStreamDestroy(ps);
     if (e == cudaSuccess) {
         if (b->is_double)
             e = b->dir < 0 ? batch_setup<double2, -1>(b->smem, &b->grid) : batch_setup<double2, 1>(b->smem, &b->grid);

@@ -569,9 +569,14 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
         cudaGetLastError();
         return FFTU_ERR_NOMEM;
     }
+    // tables and status word on a private stream: planning waits for its own work only, not for
+    // transforms in flight on other streams
+    cudaStream_t ps = nullptr;
     e = cudaMalloc(&pl->dstatus, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(pl->dstatus, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->dstatus, 0, sizeof(int), ps);
     if (e != cudaSuccess) {
+        if (ps) cudaStreamDestroy(ps);
         free_plan(pl);
         cudaGetLastError();
         set_err("status word allocation: %s", cudaGetErrorString(e));
@@ -579,8 +584,9 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
     }
     for (int l = 0; l < d && e == cudaSuccess; ++l)
         e = launch_twiddle_table(static_cast<char *>(pl->tables) + pl->table_off[l] * pl->esize, n[l],
-                                 dtype == FFTU_C128, 0);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+                                 dtype == FFTU_C128, ps);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
+    cudaStreamDestroy(ps);
     if (e != cudaSuccess) {
         free_plan(pl);
         return cuda_fail(e, "twiddle table generation");

@@ -72,6 +72,7 @@ struct Instance {
     cudaGraphExec_t gexec = nullptr;
     std::vector<cudaGraphNode_t> h2d, d2h;
     bool graph_failed = false;
+    int piece_mib = 0;
     bool busy = false;
     std::vector<Req> reqs;
     double t_start = 0;
@@ -99,8 +100,9 @@ struct fftu_server_st {
     fftu_server_config cfg;
     int device = 0;
     Clock::time_point t0;
-    std::vector<cudaStream_t> streams;
-    int next_stream = 0;
+    std::vector<cudaStream_t> streams;  // [0, split): batched instances, [split, size): solo ones
+    int split = 0;
+    int next_small = 0, next_large = 0;
 
     std::mutex in_mu;              // inbox and counters shared with submitters
     std::condition_variable in_cv;
@@ -246,6 +248,7 @@ Instance *new_instance(fftu_server_st *S, KeyState *ks, int k, bool large, fftu_
     in->ks = ks;
     in->k = k;
     in->large = large;
+    in->piece_mib = S->cfg.copy_piece_mib;
     in->slot_bytes = ((size_t)ks->N * ks->esize + 255) / 256 * 256;
     size_t bytes = 2 * (size_t)k * in->slot_bytes;
     if (large) {
@@ -289,8 +292,16 @@ Instance *new_instance(fftu_server_st *S, KeyState *ks, int k, bool large, fftu_
         }
     }
     cudaEventCreateWithFlags(&in->done, cudaEventDisableTiming);
-    in->stream = S->streams[S->next_stream];
-    S->next_stream = (S->next_stream + 1) % (int)S->streams.size();
+    // solo (large) requests get their own streams, so that a small batch never waits in a stream
+    // behind a large request's copies
+    const int ns = (int)S->streams.size();
+    if (large && S->split < ns) {
+        in->stream = S->streams[S->split + S->next_large];
+        S->next_large = (S->next_large + 1) % (ns - S->split);
+    } else {
+        in->stream = S->streams[S->next_small];
+        S->next_small = (S->next_small + 1) % (S->split > 0 ? S->split : ns);
+    }
     in->bytes = bytes;
     S->used += bytes;
     Instance *raw = in.get();
@@ -309,16 +320,34 @@ fftu_status compute(Instance *in, cudaStream_t st) {
     return fftu_batch_exec(in->batch, ins.data(), outs.data(), st);
 }
 
+// Host copies of one array: one piece, or pieces of copy_piece_mib MiB issued in order.
+size_t piece_bytes(const Instance *in, size_t bytes) {
+    return in->piece_mib > 0 ? std::min(bytes, (size_t)in->piece_mib << 20) : bytes;
+}
+
+int pieces(const Instance *in, size_t bytes) {
+    const size_t pb = piece_bytes(in, bytes);
+    return (int)((bytes + pb - 1) / pb);
+}
+
 bool build_graph(Instance *in) {
     const size_t bytes = (size_t)in->ks->N * in->ks->esize;
+    const size_t kCopyPiece = piece_bytes(in, bytes);
+    const int c = pieces(in, bytes);
     cudaGraph_t g = nullptr, child = nullptr;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
     bool ok = true;
-    in->h2d.assign(in->k, nullptr);
-    in->d2h.assign(in->k, nullptr);
+    in->h2d.assign((size_t)in->k * c, nullptr);
+    in->d2h.assign((size_t)in->k * c, nullptr);
     for (int i = 0; ok && i < in->k; ++i)
-        ok = cudaGraphAddMemcpyNode1D(&in->h2d[i], g, nullptr, 0, in->in_slot(i), in->reqs[i].r.in, bytes,
-                                      cudaMemcpyHostToDevice) == cudaSuccess;
+        for (int j = 0; ok && j < c; ++j) {
+            const size_t off = (size_t)j * kCopyPiece, len = std::min(kCopyPiece, bytes - off);
+            cudaGraphNode_t *prev = j > 0 ? &in->h2d[(size_t)i * c + j - 1] : nullptr;
+            ok = cudaGraphAddMemcpyNode1D(&in->h2d[(size_t)i * c + j], g, prev, prev ? 1 : 0,
+                                          static_cast<char *>(in->in_slot(i)) + off,
+                                          static_cast<const char *>(in->reqs[i].r.in) + off, len,
+                                          cudaMemcpyHostToDevice) == cudaSuccess;
+        }
     if (ok) {
         ok = cudaStreamBeginCapture(in->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
         if (ok) {
@@ -327,10 +356,16 @@ bool build_graph(Instance *in) {
         }
     }
     cudaGraphNode_t cn = nullptr;
-    if (ok) ok = cudaGraphAddChildGraphNode(&cn, g, in->h2d.data(), in->k, child) == cudaSuccess;
+    if (ok) ok = cudaGraphAddChildGraphNode(&cn, g, in->h2d.data(), in->h2d.size(), child) == cudaSuccess;
     for (int i = 0; ok && i < in->k; ++i)
-        ok = cudaGraphAddMemcpyNode1D(&in->d2h[i], g, &cn, 1, in->reqs[i].r.out, in->out_slot(i), bytes,
-                                      cudaMemcpyDeviceToHost) == cudaSuccess;
+        for (int j = 0; ok && j < c; ++j) {
+            const size_t off = (size_t)j * kCopyPiece, len = std::min(kCopyPiece, bytes - off);
+            cudaGraphNode_t *prev = j > 0 ? &in->d2h[(size_t)i * c + j - 1] : &cn;
+            ok = cudaGraphAddMemcpyNode1D(&in->d2h[(size_t)i * c + j], g, prev, 1,
+                                          static_cast<char *>(in->reqs[i].r.out) + off,
+                                          static_cast<const char *>(in->out_slot(i)) + off, len,
+                                          cudaMemcpyDeviceToHost) == cudaSuccess;
+        }
     if (child) cudaGraphDestroy(child);
     if (ok) ok = cudaGraphInstantiate(&in->gexec, g, 0) == cudaSuccess;
     if (!ok) {
@@ -371,12 +406,21 @@ void launch(fftu_server_st *S, Instance *in) {
         }
         if (in->gexec) {
             bool ok = true;
-            for (int i = 0; ok && i < in->k; ++i) {
-                ok = cudaGraphExecMemcpyNodeSetParams1D(in->gexec, in->h2d[i], in->in_slot(i), in->reqs[i].r.in, bytes,
-                                                       cudaMemcpyHostToDevice) == cudaSuccess &&
-                     cudaGraphExecMemcpyNodeSetParams1D(in->gexec, in->d2h[i], in->reqs[i].r.out, in->out_slot(i),
-                                                       bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
-            }
+            const size_t kCopyPiece = piece_bytes(in, bytes);
+            const int c = pieces(in, bytes);
+            for (int i = 0; ok && i < in->k; ++i)
+                for (int j = 0; ok && j < c; ++j) {
+                    const size_t off = (size_t)j * kCopyPiece, len = std::min(kCopyPiece, bytes - off);
+                    const size_t q = (size_t)i * c + j;
+                    ok = cudaGraphExecMemcpyNodeSetParams1D(in->gexec, in->h2d[q],
+                                                           static_cast<char *>(in->in_slot(i)) + off,
+                                                           static_cast<const char *>(in->reqs[i].r.in) + off, len,
+                                                           cudaMemcpyHostToDevice) == cudaSuccess &&
+                         cudaGraphExecMemcpyNodeSetParams1D(in->gexec, in->d2h[q],
+                                                           static_cast<char *>(in->reqs[i].r.out) + off,
+                                                           static_cast<const char *>(in->out_slot(i)) + off, len,
+                                                           cudaMemcpyDeviceToHost) == cudaSuccess;
+                }
             if (ok) ok = cudaGraphLaunch(in->gexec, in->stream) == cudaSuccess;
             if (ok) {
                 graphed = true;
@@ -574,7 +618,7 @@ fftu_status fftu_server_create(const fftu_server_config *cfg, fftu_server *out) 
     fftu_server_config c;
     std::memset(&c, 0, sizeof(c));
     if (cfg) c = *cfg;
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 5; ++i)
         if (c.reserved[i]) {
             fftu::record_error("server: reserved config fields must be zero");
             return FFTU_ERR_ARG;
@@ -584,7 +628,7 @@ fftu_status fftu_server_create(const fftu_server_config *cfg, fftu_server *out) 
     if (c.large_elems == 0) c.large_elems = 1ll << 22;
     if (c.max_inflight == 0) c.max_inflight = 2 * c.streams;
     if (c.max_batch < 1 || c.max_batch > 128 || c.streams < 1 || c.streams > 16 || c.large_elems < 1 ||
-        c.device_bytes < 0 || c.max_inflight < 1 || c.max_inflight > 256) {
+        c.device_bytes < 0 || c.max_inflight < 1 || c.max_inflight > 256 || c.copy_piece_mib < 0) {
         fftu::record_error("server: max_batch must be in [1, 128], streams in [1, 16], max_inflight in [1, 256], "
                            "large_elems >= 1");
         return FFTU_ERR_ARG;
@@ -620,6 +664,7 @@ fftu_status fftu_server_create(const fftu_server_config *cfg, fftu_server *out) 
         }
         S->streams.push_back(s);
     }
+    S->split = c.streams >= 2 ? c.streams / 2 : c.streams;
     S->thread = std::thread(server_main, S);
     *out = S;
     return FFTU_OK;

@@ -75,7 +75,7 @@ def test_bad_dtype_dir_and_d():
 def test_server_config_validation():
     """Invalid server configs are refused before any CUDA call; bad handles are reported."""
     import paper_2203_11795_gb300 as f
-    for cfg in ({"max_batch": 200}, {"streams": 17}, {"max_batch": -1}, {"max_inflight": 300}):
+    for cfg in ({"max_batch": 200}, {"streams": 17}, {"max_batch": -1}, {"max_inflight": 300}, {"copy_piece_mib": -1}):
         with pytest.raises(f.FFTUError) as ei:
             f.fftu_server_create(**cfg)
         assert ei.value.status == 1
