@@ -12,6 +12,18 @@ namespace fftu {
 // complex values a thread holds per stage: 16 (c64) or 8 (c128)
 template <typename C> __host__ __device__ constexpr int ept() { return sizeof(C) == 8 ? kEptMax : kEptMax / 2; }
 
+// Global -> shared copy of one element without a register round trip (cp.async): a thread can
+// have all of its tile's loads in flight at once.  Completed by async_copy_wait() + __syncthreads().
+template <typename C> __device__ __forceinline__ void async_copy(C *dst_shared, const C *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_shared);
+    if constexpr (sizeof(C) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void async_copy_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 
 template <typename C, int DIR, int R>
 __device__ __forceinline__ void stockham_stage(C *sm, const C *__restrict__ tw, const AxisPass &a, int Ns,
@@ -100,8 +112,9 @@ __device__ __forceinline__ void axis_tile(const AxisPass &a, int64_t t, C *sm, c
         }
         const int64_t gp = c0 + (lp & (a.Gt - 1)) + ((int64_t)(lp >> a.lg_Gt) << a.lg_G);
         const int64_t g = a.contiguous ? gbase + (int64_t)v * a.nl + gp : gbase + gp * a.inner + v;
-        sm[e] = src[g];
+        async_copy(sm + e, src + g);
     }
+    async_copy_wait();
     __syncthreads();
 
     int Ns = 1;
@@ -182,8 +195,9 @@ __device__ __forceinline__ void phaseb_tile(const PhaseBFused &b, int64_t t, C *
             sf >>= b.lg_p[l];
             g += (int64_t)sl * b.L[l] * b.stride[l];
         }
-        sm[e] = data[g];
+        async_copy(sm + e, data + g);
     }
+    async_copy_wait();
     __syncthreads();
     int S = b.Mt;
     for (int l = d - 1; l >= 0; --l) {
