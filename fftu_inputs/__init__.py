@@ -26,7 +26,7 @@ _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 _CHUNK = 1 << 22
 
-__all__ = ["splitmix64", "uniform_pm1", "complex_uniform", "complex_uniform_range"]
+__all__ = ["splitmix64", "uniform_pm1", "complex_uniform", "complex_uniform_range", "complex_loguniform"]
 
 
 def splitmix64(seed: int, counters: np.ndarray) -> np.ndarray:
@@ -70,3 +70,26 @@ def complex_uniform(seed: int, shape, dtype=np.complex128) -> np.ndarray:
     shape = tuple(int(s) for s in shape)
     n = int(np.prod(shape)) if shape else 1
     return complex_uniform_range(seed, 0, n, dtype).reshape(shape)
+
+
+def complex_loguniform(seed: int, shape, lo: float = 1e-3, hi: float = 1e3, dtype=np.complex128) -> np.ndarray:
+    """Row-major array whose magnitudes are log-uniform in [lo, hi) and phases uniform.
+
+    Element j: u = the (counter 2j, 2j + 1) pair mapped to [0, 1) as in complex_uniform;
+    magnitude 10^(log10 lo + u_0 (log10 hi - log10 lo)), phase 2 pi u_1.  The wide dynamic
+    range tests arithmetic whose 16-bit operands need scaling.
+    """
+    shape = tuple(int(s) for s in shape)
+    n = int(np.prod(shape)) if shape else 1
+    out = np.empty(n, dtype=dtype)
+    a, b = np.log10(lo), np.log10(hi)
+    pos = 0
+    while pos < n:
+        m = min(_CHUNK, n - pos)
+        ctr = np.arange(2 * pos, 2 * (pos + m), dtype=np.uint64)
+        u = 0.5 * (uniform_pm1(seed, ctr) + 1.0)
+        mag = 10.0 ** (a + (b - a) * u[0::2])
+        ph = 2.0 * np.pi * u[1::2]
+        out[pos: pos + m] = mag * np.cos(ph) + 1j * (mag * np.sin(ph))
+        pos += m
+    return out.reshape(shape)

@@ -71,13 +71,30 @@ typedef enum {
 
 /* Kernel schedule.  AUTO picks the fastest schedule the plan supports;
  * GENERIC forces one strided pass per axis for each phase (any d, any
- * power-of-two shape) and is kept as a cross-check of the fused kernels. */
-typedef enum { FFTU_SCHED_AUTO = 0, FFTU_SCHED_GENERIC = 1, FFTU_SCHED_FUSED = 2 } fftu_schedule;
+ * power-of-two shape) and is kept as a cross-check of the fused kernels;
+ * GENERIC_A uses the strided passes for phase A only (phase B as AUTO). */
+typedef enum {
+    FFTU_SCHED_AUTO = 0,
+    FFTU_SCHED_GENERIC = 1,
+    FFTU_SCHED_FUSED = 2,
+    FFTU_SCHED_GENERIC_A = 3
+} fftu_schedule;
+
+/* Arithmetic of the radix-16 DFT stages of the strided passes (complex64 plans only).
+ * NATIVE: FP32 (complex64) or FP64 (complex128) on the CUDA cores.
+ * SPLIT_BF16 / SPLIT_FP16: each radix-16 stage of 8 butterflies is a real 32 x 32 contraction on
+ * the tensor cores (mma.sync m16n8k16, FP32 accumulation) with both operands split into a 16-bit
+ * high and low part (three products; the low x low term is dropped); FP16 operands are scaled per
+ * group of 8 butterflies by a power of two.  Twiddles, the remaining radix-2/4/8 stage and phase B
+ * stay FP32.  Implies the GENERIC_A schedule.  Relative error per stage about 3 u^2 (u = 2^-8 for
+ * bfloat16, 2^-11 for float16), against about 2^-24 for FP32. */
+typedef enum { FFTU_PREC_NATIVE = 0, FFTU_PREC_SPLIT_BF16 = 1, FFTU_PREC_SPLIT_FP16 = 2 } fftu_precision;
 
 typedef struct {
     int schedule;        /* fftu_schedule */
     int tune;            /* with p == NULL: time candidate grids at plan time and keep the fastest */
-    int reserved[6];     /* must be zero */
+    int precision;       /* fftu_precision */
+    int reserved[5];     /* must be zero */
 } fftu_options;
 
 typedef struct {
@@ -94,7 +111,7 @@ typedef struct {
     int64_t table_bytes;       /* device bytes of twiddle tables owned by the plan */
     int64_t workspace_bytes;   /* device bytes of workspace owned by the plan */
     int tuned;                 /* 1 when p was chosen by measurement (fftu_options.tune) */
-    int reserved_info;
+    int precision;             /* fftu_precision of the radix-16 stages */
 } fftu_info;
 
 /*

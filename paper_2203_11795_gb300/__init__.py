@@ -22,7 +22,8 @@ FFTU_MAX_DIMS = 8
 FFTU_C64, FFTU_C128 = 1, 2
 FFTU_FORWARD, FFTU_INVERSE = -1, 1
 FFTU_PHASE_A, FFTU_PHASE_B, FFTU_PHASE_ALL = 1, 2, 3
-FFTU_SCHED_AUTO, FFTU_SCHED_GENERIC, FFTU_SCHED_FUSED = 0, 1, 2
+FFTU_SCHED_AUTO, FFTU_SCHED_GENERIC, FFTU_SCHED_FUSED, FFTU_SCHED_GENERIC_A = 0, 1, 2, 3
+FFTU_PREC_NATIVE, FFTU_PREC_SPLIT_BF16, FFTU_PREC_SPLIT_FP16 = 0, 1, 2
 STATUS_NAMES = {0: "FFTU_OK", 1: "FFTU_ERR_ARG", 2: "FFTU_ERR_DIVISIBILITY", 3: "FFTU_ERR_UNSUPPORTED",
                 4: "FFTU_ERR_NOMEM", 5: "FFTU_ERR_CUDA", 6: "FFTU_ERR_TIMEOUT", 7: "FFTU_ERR_INTERNAL"}
 
@@ -45,7 +46,8 @@ class FFTUError(RuntimeError):
 
 
 class fftu_options(ctypes.Structure):
-    _fields_ = [("schedule", ctypes.c_int), ("tune", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+    _fields_ = [("schedule", ctypes.c_int), ("tune", ctypes.c_int), ("precision", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class fftu_info(ctypes.Structure):
@@ -53,7 +55,7 @@ class fftu_info(ctypes.Structure):
                 ("dtype", ctypes.c_int), ("dir", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("launches_phase_a", ctypes.c_int), ("launches_phase_b", ctypes.c_int),
                 ("N", ctypes.c_int64), ("alg_bytes", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
-                ("workspace_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("reserved_info", ctypes.c_int)]
+                ("workspace_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 class fftu_server_config(ctypes.Structure):
@@ -159,9 +161,9 @@ def fftu_plan(d: int, n, p, dtype: int, direction: int) -> int:
 
 
 def fftu_plan_ex(d: int, n, p, dtype: int, direction: int, schedule: int = FFTU_SCHED_AUTO,
-                 tune: bool = False) -> int:
+                 tune: bool = False, precision: int = FFTU_PREC_NATIVE) -> int:
     h = ctypes.c_void_p()
-    opts = fftu_options(schedule=int(schedule), tune=int(bool(tune)))
+    opts = fftu_options(schedule=int(schedule), tune=int(bool(tune)), precision=int(precision))
     _check(_lib.fftu_plan_ex(int(d), _i64(n), _i64(p), int(dtype), int(direction), ctypes.byref(opts),
                              ctypes.byref(h)), "fftu_plan_ex")
     return h.value
@@ -192,7 +194,8 @@ def fftu_plan_info(plan: int) -> dict:
     return {"d": d, "n": list(info.n[:d]), "p": list(info.p[:d]), "dtype": info.dtype, "dir": info.dir,
             "schedule": info.schedule, "launches_phase_a": info.launches_phase_a,
             "launches_phase_b": info.launches_phase_b, "N": info.N, "alg_bytes": info.alg_bytes,
-            "table_bytes": info.table_bytes, "workspace_bytes": info.workspace_bytes, "tuned": info.tuned}
+            "table_bytes": info.table_bytes, "workspace_bytes": info.workspace_bytes, "tuned": info.tuned,
+            "precision": info.precision}
 
 
 def fftu_check_device_status(plan: int) -> None:
@@ -307,14 +310,14 @@ class Plan:
     """A plan for one shape, cyclic grid p, dtype and direction (fftu_plan)."""
 
     def __init__(self, n, p=None, dtype=None, inverse: bool = False, schedule: int = FFTU_SCHED_AUTO,
-                 tune: bool = False):
+                 tune: bool = False, precision: int = FFTU_PREC_NATIVE):
         import torch
         self.n = tuple(int(v) for v in n)
         self.dtype = dtype if dtype is not None else torch.complex64
         code = _dtype_code(self.dtype)
         self.inverse = bool(inverse)
         self.handle = fftu_plan_ex(len(self.n), self.n, None if p is None else list(p), code,
-                                   FFTU_INVERSE if inverse else FFTU_FORWARD, schedule, tune)
+                                   FFTU_INVERSE if inverse else FFTU_FORWARD, schedule, tune, precision)
         self.info = fftu_plan_info(self.handle)
         self.p = tuple(self.info["p"])
 

@@ -27,15 +27,16 @@ namespace {
 
 constexpr int kAxisThreads = 512;
 
-// R0: radix of the first stage (1 = none); every later stage is radix 8.
-template <typename C, int DIR, int R0>
+// R0: radix of the first stage (1 = none); every later stage is radix 8.  With TCK (split-precision
+// tensor-core radix-16 stages, complex64 only), R0 is the radix of the last, CUDA-core stage.
+template <typename C, int DIR, int R0, int TCK = 0>
 __global__ void __launch_bounds__(kAxisThreads) axis_pass_kernel(const __grid_constant__ AxisPass a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
     const C *__restrict__ src = static_cast<const C *>(a.src);
     C *__restrict__ dst = static_cast<C *>(a.dst);
     const C *__restrict__ tw = static_cast<const C *>(a.tw);
-    for (int64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) axis_tile<C, DIR, R0>(a, t, sm, src, dst, tw);
+    for (int64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) axis_tile<C, DIR, R0, TCK>(a, t, sm, src, dst, tw);
 }
 
 // w_n^e = exp(-2 pi i e / n) for e in [n], evaluated in FP64 by sincospi on the
@@ -58,10 +59,31 @@ __global__ void pointwise_kernel(C *out, const C *mul, int64_t n) {
         out[i] = cmul(out[i], mul[i]);
 }
 
+template <int DIR, int TCK>
+void launch_axis_tc(const AxisPass &a, unsigned grid, size_t smem, cudaStream_t st) {
+    const int last = a.nstages > 0 ? a.radix[a.nstages - 1] : 1;
+    switch (last) {
+        case 2: axis_pass_kernel<float2, DIR, 2, TCK><<<grid, a.threads, smem, st>>>(a); break;
+        case 4: axis_pass_kernel<float2, DIR, 4, TCK><<<grid, a.threads, smem, st>>>(a); break;
+        case 8: axis_pass_kernel<float2, DIR, 8, TCK><<<grid, a.threads, smem, st>>>(a); break;
+        default: axis_pass_kernel<float2, DIR, 1, TCK><<<grid, a.threads, smem, st>>>(a); break;
+    }
+}
+
 template <typename C, int DIR>
 cudaError_t launch_axis_t(const AxisPass &a, cudaStream_t st) {
     size_t smem = (size_t)a.tile * sizeof(C);
     int64_t grid = a.tiles < (int64_t)1 << 30 ? a.tiles : (int64_t)1 << 30;
+    if constexpr (sizeof(C) == 8) {
+        if (a.tc == 1) {
+            launch_axis_tc<DIR, 1>(a, (unsigned)grid, smem, st);
+            return cudaGetLastError();
+        }
+        if (a.tc == 2) {
+            launch_axis_tc<DIR, 2>(a, (unsigned)grid, smem, st);
+            return cudaGetLastError();
+        }
+    }
     const int r0 = a.nstages > 0 && a.radix[0] != 8 ? a.radix[0] : 1;
     switch (r0) {
         case 2: axis_pass_kernel<C, DIR, 2><<<(unsigned)grid, a.threads, smem, st>>>(a); break;
@@ -72,9 +94,9 @@ cudaError_t launch_axis_t(const AxisPass &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <typename C, int DIR, int R0>
+template <typename C, int DIR, int R0, int TCK = 0>
 cudaError_t prepare_axis_r() {
-    return cudaFuncSetAttribute(axis_pass_kernel<C, DIR, R0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(axis_pass_kernel<C, DIR, R0, TCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kMaxDynSmem);
 }
 
@@ -84,6 +106,16 @@ cudaError_t prepare_axis_t() {
     if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 2>();
     if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 4>();
     if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 16>();
+    if constexpr (sizeof(C) == 8) {
+        if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 1, 1>();
+        if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 2, 1>();
+        if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 4, 1>();
+        if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 8, 1>();
+        if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 1, 2>();
+        if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 2, 2>();
+        if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 4, 2>();
+        if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 8, 2>();
+    }
     return e;
 }
 

@@ -197,6 +197,10 @@ fftu_status batch_create(int count, const fftu_handle *plans, Batch **out_batch)
             record_error("batch: every plan needs the same dtype, direction and device");
             return FFTU_ERR_ARG;
         }
+        if (views[i].precision != 0) {
+            record_error("batch: split-precision plans are not batched");
+            return FFTU_ERR_UNSUPPORTED;
+        }
         if (views[i].pingpong) {
             record_error("batch: plans whose phase A alternates with a workspace (long lines) are not batched");
             return FFTU_ERR_UNSUPPORTED;

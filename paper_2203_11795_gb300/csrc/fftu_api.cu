@@ -71,6 +71,15 @@ int radix_plan(int len, int *radix) {
     return n;
 }
 
+// Radix sequence of the split-precision passes: radix-16 stages (tensor cores), then one stage of
+// the remaining factor 2, 4 or 8 (CUDA cores).
+int radix_plan_tc(int len, int *radix) {
+    int k = ilog2(len), n = 0;
+    for (; k >= 4; k -= 4) radix[n++] = 16;
+    if (k > 0) radix[n++] = 1 << k;
+    return n;
+}
+
 enum StepKind { STEP_AXIS = 1, STEP_PHASE_B_FUSED = 2, STEP_PHASE_B3 = 3, STEP_PHASE_A3 = 4 };
 
 struct Step {
@@ -93,7 +102,7 @@ struct Plan {
     int d = 0;
     int64_t n[FFTU_MAX_DIMS] = {};
     int64_t p[FFTU_MAX_DIMS] = {};
-    int dtype = 0, dir = 0, device = 0, schedule = 0;
+    int dtype = 0, dir = 0, device = 0, schedule = 0, precision = 0;
     int64_t N = 0;
     size_t esize = 0;
     void *tables = nullptr;
@@ -177,7 +186,8 @@ fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPa
     a.threads = th;
     a.tw = pl.table(l);
     a.scale = scale;
-    a.nstages = radix_plan(a.len, a.radix);
+    a.tc = pl.precision;
+    a.nstages = a.tc ? radix_plan_tc(a.len, a.radix) : radix_plan(a.len, a.radix);
     return FFTU_OK;
 }
 
@@ -291,7 +301,7 @@ fftu_status build_fused_phase_a(Plan &pl, bool *used) {
 fftu_status build_schedule(Plan &pl, int sched) {
     const double scale = pl.dir == FFTU_INVERSE ? 1.0 / (double)pl.N : 1.0;
     bool fused_a = false;
-    if (sched != FFTU_SCHED_GENERIC) {
+    if (sched != FFTU_SCHED_GENERIC && sched != FFTU_SCHED_GENERIC_A) {
         fftu_status st = build_fused_phase_a(pl, &fused_a);
         if (st != FFTU_OK) return st;
     }
@@ -343,7 +353,8 @@ fftu_status build_schedule(Plan &pl, int sched) {
             pl.phase_b.push_back(t);
         }
     }
-    pl.schedule = sched == FFTU_SCHED_GENERIC ? FFTU_SCHED_GENERIC : FFTU_SCHED_FUSED;
+    pl.schedule = sched == FFTU_SCHED_GENERIC ? FFTU_SCHED_GENERIC
+                  : sched == FFTU_SCHED_GENERIC_A ? FFTU_SCHED_GENERIC_A : FFTU_SCHED_FUSED;
     return FFTU_OK;
 }
 
@@ -425,6 +436,7 @@ fftu_status plan_view(fftu_handle h, PlanView *v) {
     v->dir = pl.dir;
     v->device = pl.device;
     v->pingpong = pl.generic_pingpong;
+    v->precision = pl.precision;
     v->a_passes.clear();
     v->b_steps.clear();
     const bool fused_a = !pl.phase_a.empty() && pl.phase_a[0].kind == STEP_PHASE_A3;
@@ -480,9 +492,25 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
         return FFTU_ERR_ARG;
     }
     int sched = opts ? opts->schedule : FFTU_SCHED_AUTO;
-    if (sched < FFTU_SCHED_AUTO || sched > FFTU_SCHED_FUSED) {
+    if (sched < FFTU_SCHED_AUTO || sched > FFTU_SCHED_GENERIC_A) {
         set_err("unknown schedule %d", sched);
         return FFTU_ERR_ARG;
+    }
+    const int precision = opts ? opts->precision : FFTU_PREC_NATIVE;
+    if (precision < FFTU_PREC_NATIVE || precision > FFTU_PREC_SPLIT_FP16) {
+        set_err("unknown precision %d", precision);
+        return FFTU_ERR_ARG;
+    }
+    if (precision != FFTU_PREC_NATIVE) {
+        if (dtype != FFTU_C64) {
+            set_err("split-precision tensor-core stages are for complex64 plans");
+            return FFTU_ERR_UNSUPPORTED;
+        }
+        if (sched == FFTU_SCHED_FUSED) {
+            set_err("split-precision stages run in the strided passes: use AUTO, GENERIC or GENERIC_A");
+            return FFTU_ERR_ARG;
+        }
+        if (sched == FFTU_SCHED_AUTO) sched = FFTU_SCHED_GENERIC_A;
     }
     if (opts)
         for (int r : opts->reserved)
@@ -548,6 +576,7 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
     pl->dtype = dtype;
     pl->dir = dir;
     pl->tuned = tuned;
+    pl->precision = precision;
     pl->N = N;
     pl->esize = dtype == FFTU_C128 ? 16 : 8;
     cudaError_t e = cudaGetDevice(&pl->device);
@@ -784,6 +813,7 @@ fftu_status fftu_plan_info(fftu_handle h, fftu_info *info) {
     info->table_bytes = (int64_t)pl->table_bytes;
     info->workspace_bytes = (int64_t)pl->workspace_bytes;
     info->tuned = pl->tuned;
+    info->precision = pl->precision;
     return FFTU_OK;
 }
 

@@ -44,6 +44,7 @@ struct AxisPass {
     int nstages;
     int radix[kMaxStages];
     int64_t tiles;
+    int tc;           // 0: CUDA-core stages; 1 / 2: radix-16 stages as split bfloat16 / float16 MMAs
 };
 
 // Phase B on the d-dim groups {m + s' (n/p)} with every p_l <= 16, in one pass.
@@ -98,6 +99,7 @@ struct StepView {
 struct PlanView {
     int dtype, dir, device;
     bool pingpong;                  // phase A alternates with a workspace (long lines)
+    int precision;                  // fftu_precision of the plan's radix-16 stages
     std::vector<StepView> a_passes;  // phase A, generic passes (first reads in, then in place on out)
     std::vector<StepView> b_steps;   // phase B, in place on out
 };

@@ -84,3 +84,14 @@ def test_server_config_validation():
     with pytest.raises(f.FFTUError):
         f.fftu_server_poll(None, 4)
     f.fftu_server_destroy(None)
+
+
+def test_precision_option_validation():
+    """Unknown precision values are refused before any device work."""
+    import paper_2203_11795_gb300 as f
+    with pytest.raises(f.FFTUError) as ei:
+        f.fftu_plan_ex(3, [64, 64, 64], None, f.FFTU_C64, f.FFTU_FORWARD, precision=7)
+    assert ei.value.status == 1
+    with pytest.raises(f.FFTUError) as ei:
+        f.fftu_plan_ex(3, [64, 64, 64], None, f.FFTU_C64, f.FFTU_FORWARD, schedule=9)
+    assert ei.value.status == 1

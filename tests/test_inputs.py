@@ -31,3 +31,17 @@ def test_complex64_is_rounded_fp64_draw():
     s = complex_uniform(5, (257,), dtype=np.complex64)
     assert s.dtype == np.complex64
     assert np.array_equal(s, d.astype(np.complex64))
+
+
+def test_loguniform_range_and_determinism():
+    from fftu_inputs import complex_loguniform
+    x = complex_loguniform(5, (64, 64), dtype=np.complex128)
+    y = complex_loguniform(5, (64, 64), dtype=np.complex128)
+    assert np.array_equal(x, y)
+    mag = np.abs(x)
+    assert mag.min() >= 1e-3 * (1 - 1e-12) and mag.max() < 1e3
+    # log-uniform: each decade holds about a sixth of the values
+    hist = np.histogram(np.log10(mag), bins=6, range=(-3, 3))[0]
+    assert hist.min() > 0.8 * x.size / 6
+    z = complex_loguniform(5, (64, 64), dtype=np.complex64)
+    assert z.dtype == np.complex64 and np.allclose(z, x.astype(np.complex64))
