@@ -154,13 +154,13 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const __grid_const
 }
 
 template <typename C, int DIR>
-cudaError_t batch_setup(size_t smem, int *grid) {
+cudaError_t batch_setup(size_t smem, int threads, int *grid) {
     cudaError_t e = cudaFuncSetAttribute(batch_kernel<C, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<C, DIR>, kBatchThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<C, DIR>, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     *grid = sms * per_sm;
@@ -171,6 +171,7 @@ cudaError_t batch_setup(size_t smem, int *grid) {
 
 struct Batch {
     int count = 0, is_double = 0, dir = 0, device = 0, grid = 0;
+    int threads = kBatchThreads;  // the largest block any job's tile needs (a multiple of 32, <= 512)
     size_t smem = 0;
     int njobs = 0;
     int64_t total = 0;
@@ -212,6 +213,7 @@ fftu_status batch_create(int count, const fftu_handle *plans, Batch **out_batch)
     size_t max_tile_bytes = 0;
     const size_t esize = views[0].dtype == FFTU_C128 ? 16 : 8;
     int max_passes = 0;
+    int max_threads = 128;  // phase-B tiles loop over any block size
     for (auto &v : views) max_passes = std::max(max_passes, (int)(v.a_passes.size() + v.b_steps.size()));
     for (int k = 0; k < max_passes; ++k) {
         for (int i = 0; i < count; ++i) {
@@ -231,6 +233,7 @@ fftu_status batch_create(int count, const fftu_handle *plans, Batch **out_batch)
                 J.tiles = sv.axis.tiles;
                 J.reads_input = k == 0;
                 max_tile_bytes = std::max(max_tile_bytes, (size_t)sv.axis.tile * esize);
+                max_threads = std::max(max_threads, sv.axis.threads);
             } else {
                 J.kind = 2;
                 J.b = sv.pb;
@@ -271,6 +274,7 @@ fftu_status batch_create(int count, const fftu_handle *plans, Batch **out_batch)
     b->njobs = (int)jobs.size();
     b->total = first;
     b->smem = max_tile_bytes;
+    b->threads = std::min(kBatchThreads, (max_threads + 31) / 32 * 32);
     const size_t jb = sizeof(BatchJob) * jobs.size(), fb = sizeof(int64_t) * jobs.size();
     b->counter_bytes = 16 + sizeof(unsigned) * jobs.size();
     const size_t bytes = jb + fb + b->counter_bytes + 16;
@@ -297,9 +301,11 @@ fftu_status batch_create(int count, const fftu_handle *plans, Batch **out_batch)
     if (ps) cudaStreamDestroy(ps);
     if (e == cudaSuccess) {
         if (b->is_double)
-            e = b->dir < 0 ? batch_setup<double2, -1>(b->smem, &b->grid) : batch_setup<double2, 1>(b->smem, &b->grid);
+            e = b->dir < 0 ? batch_setup<double2, -1>(b->smem, b->threads, &b->grid)
+                           : batch_setup<double2, 1>(b->smem, b->threads, &b->grid);
         else
-            e = b->dir < 0 ? batch_setup<float2, -1>(b->smem, &b->grid) : batch_setup<float2, 1>(b->smem, &b->grid);
+            e = b->dir < 0 ? batch_setup<float2, -1>(b->smem, b->threads, &b->grid)
+                           : batch_setup<float2, 1>(b->smem, b->threads, &b->grid);
     }
     if (e != cudaSuccess) {
         cudaFree(b->dev_mem);
@@ -341,14 +347,14 @@ fftu_status batch_exec(Batch *b, const void *const *ins, void *const *outs, cuda
     if (grid > b->total) grid = b->total;
     if (b->is_double) {
         if (b->dir < 0)
-            batch_kernel<double2, -1><<<(unsigned)grid, kBatchThreads, b->smem, st>>>(P);
+            batch_kernel<double2, -1><<<(unsigned)grid, b->threads, b->smem, st>>>(P);
         else
-            batch_kernel<double2, 1><<<(unsigned)grid, kBatchThreads, b->smem, st>>>(P);
+            batch_kernel<double2, 1><<<(unsigned)grid, b->threads, b->smem, st>>>(P);
     } else {
         if (b->dir < 0)
-            batch_kernel<float2, -1><<<(unsigned)grid, kBatchThreads, b->smem, st>>>(P);
+            batch_kernel<float2, -1><<<(unsigned)grid, b->threads, b->smem, st>>>(P);
         else
-            batch_kernel<float2, 1><<<(unsigned)grid, kBatchThreads, b->smem, st>>>(P);
+            batch_kernel<float2, 1><<<(unsigned)grid, b->threads, b->smem, st>>>(P);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) {

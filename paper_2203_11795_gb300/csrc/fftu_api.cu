@@ -121,6 +121,10 @@ struct Plan {
 
 namespace {
 
+// Whole-line tiles aim at this many elements: 256 threads of 16 (complex64) or 8 (complex128)
+// values, so that two CTAs share an SM at the kernels' register count.
+constexpr int64_t kTileTargetC64 = 4096, kTileTargetC128 = 2048;
+
 // Generic schedule: one strided pass per axis.  mode 0 = phase A, mode 1 = phase B.
 fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPass &a) {
     std::memset(&a, 0, sizeof(a));
@@ -129,7 +133,7 @@ fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPa
     for (int k = 0; k < l; ++k) outer *= pl.n[k];
     for (int k = l + 1; k < pl.d; ++k) inner *= pl.n[k];
     const int64_t nl = pl.n[l], Ll = pl.n[l] / pl.p[l];
-    const int64_t target = is_double ? 4096 : 8192;
+    const int64_t target = is_double ? kTileTargetC128 : kTileTargetC64;
     const int64_t maxtile = is_double ? kMaxGenericTile / 4 : kMaxGenericTile / 2;
     a.outer = outer;
     a.inner = inner;
