@@ -30,6 +30,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 8000.0  # the nominal HBM3e figure the target is also quoted against
 METRIC = "3D FFT HBM GB/s & % roofline at 512^3 c64; mixed-request p50/p99 latency"
 METRIC_DETAIL = ("value: algorithmic HBM GB/s, B_alg = 4 N b bytes per transform (b = element size), "
                  "one forward + one inverse transform per step; the mixed-request p50/p99 latency is the "
@@ -47,11 +48,13 @@ def parse_args():
     ap.add_argument("--serve", action="store_true", help="print only the serving run's line")
     ap.add_argument("--no-serve", action="store_true", help="leave the serving run out of the default line")
     ap.add_argument("--serve-requests", type=int, default=10000)
-    ap.add_argument("--serve-rate", type=float, default=1000.0, help="offered Poisson rate, requests per second")
+    ap.add_argument("--serve-rate", type=float, default=0.0,
+                    help="offered Poisson rate, requests per second (0 = 0.7 x the measured saturation rate)")
     ap.add_argument("--serve-warmup", type=int, default=400)
     ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--serve-inflight", type=int, default=0, help="0 = 2 x streams")
     ap.add_argument("--serve-piece-mib", type=int, default=0, help="host copies in pieces of this many MiB")
+    ap.add_argument("--batch-cubes", action="store_true", help="batch of cubes n^3 only (n in 32, 64, 128)")
     ap.add_argument("--batch", type=int, default=0,
                     help="K > 0: time K uneven 3D transforms (n_l in {32, 64, 128}) in one persistent launch "
                          "per direction instead of the single-array workload")
@@ -64,6 +67,7 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true", help="leave out the torch.fft (cuFFT) context timing")
     ap.add_argument("--cpu-sample", default="512,512,512", help="oracle sample shape for cpu_baseline")
     ap.add_argument("--cpu-reps", type=int, default=3, help="oracle forward+inverse repetitions for cpu_baseline")
     ap.add_argument("--ref-sample", default="256,256,256", help="oracle sample shape per reference step")
@@ -313,6 +317,29 @@ def run_ours(args):
             vs_native = float((torch.linalg.vector_norm(y - y_nat) / torch.linalg.vector_norm(y_nat)).item())
             del y_nat
 
+    # context only: the same forward + inverse through torch.fft (cuFFT), run as a library
+    cufft = None
+    if not args.no_cufft and rank == 0:
+        try:
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    torch.fft.ifftn(torch.fft.fftn(x))
+                torch.cuda.synchronize(dev)
+                c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = max(3, min(20, args.steps))
+                c0.record(stream)
+                for _ in range(reps):
+                    torch.fft.ifftn(torch.fft.fftn(x))
+                c1.record(stream)
+            torch.cuda.synchronize(dev)
+            cms = c0.elapsed_time(c1) / reps
+            cufft = {"impl": "torch.fft.fftn + ifftn (cuFFT)",
+                     "ms_per_step": cms, "value": 2 * alg_bytes(shape, esize) / (cms * 1e-3) / 1e9, "unit": "GB/s",
+                     "note": "context, not a target: cuFFT's own schedule (not the cyclic method), allocations "
+                             "included, same array and metric"}
+        except Exception as exc:
+            cufft = {"error": repr(exc)}
+
     e2e = None
     if not args.no_e2e:
         out_host = torch.empty_like(x_host).pin_memory()
@@ -350,6 +377,8 @@ def run_ours(args):
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": traffic_for(kernel_name), "kernel": dom, "launches_in_phase": launches,
                     "peak_source": f"{peak_kind} hbm_gbs",
+                    "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_gbs": NOMINAL_HBM_GBS,
+                    "step_frac": value / peak, "step_frac_of_nominal": value / NOMINAL_HBM_GBS,
                     "phase_ms": {"phase_a": ta, "phase_b": tb},
                     "phase_frac": {"phase_a": half / (ta * 1e-3) / 1e9 / peak,
                                    "phase_b": half / (tb * 1e-3) / 1e9 / peak}}
@@ -365,9 +394,19 @@ def run_ours(args):
             t_cpu, cores = oracle_cpu_run(sample, args.seed, reps=args.cpu_reps)
             cpu = {"value": 2 * alg_bytes(sample, esize) / t_cpu / 1e9, "unit": "GB/s", "cores": cores,
                    "kind": "oracle", "seconds_per_rep": t_cpu,
-                   "sample": f"FP64 oracle forward+inverse of one {'x'.join(map(str, sample))} array, "
-                             f"{args.cpu_reps} repetitions (same seeded inputs), GB/s scaled by 4*N*8 bytes "
-                             f"per transform"}
+                   "sample": f"plain FP64 oracle (not an optimized FFT), forward+inverse of one "
+                             f"{'x'.join(map(str, sample))} array, {args.cpu_reps} repetitions (same seeded "
+                             f"inputs), all {cores} host cores, GB/s scaled by 4*N*8 bytes per transform"}
+            import oracle
+            oracle.set_threads(1)
+            try:
+                one = (128, 128, 128)
+                t1, _ = oracle_cpu_run(one, args.seed, reps=3)
+            finally:
+                oracle.set_threads(0)
+            cpu["single_thread"] = {"value": 2 * alg_bytes(one, esize) / t1 / 1e9, "unit": "GB/s", "cores": 1,
+                                    "seconds_per_rep": t1,
+                                    "sample": "same oracle, 1 thread, forward+inverse of one 128^3 array, 3 reps"}
         line = {
             "metric": METRIC, "metric_detail": METRIC_DETAIL,
             "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -394,6 +433,7 @@ def run_ours(args):
             "clocks": clocks,
             "round_trip_rel_l2": rt_err,
             "forward_vs_fp32_stages_rel_l2": vs_native,
+            "cufft_context": cufft,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
@@ -415,7 +455,9 @@ def run_serving(fftu, args, local):
 
     Shapes uniform over SERVE_SHAPES, complex128 with probability 0.1, forward/inverse
     equiprobable.  Host buffers are page-locked pools per (shape, dtype), inputs seeded.
-    Latency = completion seen by the server minus submission, on the server's clock."""
+    The offered rate is --serve-rate, or (default) 0.7 x the saturation throughput measured
+    first by a closed-loop burst of the same mix.  Latency = completion seen by the server
+    minus submission, on the server's clock."""
     import threading
 
     import numpy as np
@@ -423,10 +465,11 @@ def run_serving(fftu, args, local):
     from fftu_inputs import complex_uniform
 
     rng = np.random.default_rng(args.seed + 77)
-    total = args.serve_warmup + args.serve_requests
-    kinds = [(SERVE_SHAPES[rng.integers(len(SERVE_SHAPES))], bool(rng.random() < 0.1), bool(rng.integers(2)))
-             for _ in range(total)]
-    gaps = rng.exponential(1.0 / args.serve_rate, size=total)
+
+    def draw(count):
+        return [(SERVE_SHAPES[rng.integers(len(SERVE_SHAPES))], bool(rng.random() < 0.1), bool(rng.integers(2)))
+                for _ in range(count)]
+
     pools, free = {}, {}
     t_alloc = time.perf_counter()
     for shape in SERVE_SHAPES:
@@ -442,68 +485,77 @@ def run_serving(fftu, args, local):
             pools[(shape, c128)] = slots
             free[(shape, c128)] = list(range(size))
     t_alloc = time.perf_counter() - t_alloc
-    lock = threading.Lock()
-    cv = threading.Condition(lock)
-    slot_of, meta = {}, {}
-    stalls = [0]
+    cv = threading.Condition(threading.Lock())
     server = fftu.fftu_server_create(max_batch=64, streams=args.serve_streams, max_inflight=args.serve_inflight,
                                      copy_piece_mib=args.serve_piece_mib)
 
-    def generator():
-        t_next = time.perf_counter()
-        for i in range(total):
-            t_next += gaps[i]
-            while True:
-                dt_ = t_next - time.perf_counter()
-                if dt_ <= 0:
-                    break
-                time.sleep(dt_ if dt_ > 2e-4 else 0)
-            shape, c128, inverse = kinds[i]
-            key = (shape, c128)
-            with cv:
-                if not free[key]:
-                    stalls[0] += 1
-                while not free[key]:
-                    cv.wait(0.01)
-                j = free[key].pop()
-                slot_of[i] = (key, j)
-            xi, yi = pools[key][j]
-            meta[i] = (shape, c128, inverse)
-            fftu.fftu_server_submit(server, shape, fftu.FFTU_C128 if c128 else fftu.FFTU_C64,
-                                    fftu.FFTU_INVERSE if inverse else fftu.FFTU_FORWARD, xi.data_ptr(),
-                                    yi.data_ptr(), i)
+    def phase(kinds, gaps, tag0):
+        """Submit kinds[i] at the cumulative gaps (None: as soon as a buffer is free); wait for all."""
+        slot_of, meta, stalls, done = {}, {}, [0], []
 
-    done = []
-    gen = threading.Thread(target=generator)
+        def generator():
+            t_next = time.perf_counter()
+            for i, (shape, c128, inverse) in enumerate(kinds):
+                if gaps is not None:
+                    t_next += gaps[i]
+                    while True:
+                        dt_ = t_next - time.perf_counter()
+                        if dt_ <= 0:
+                            break
+                        time.sleep(dt_ if dt_ > 2e-4 else 0)
+                key = (shape, c128)
+                with cv:
+                    if not free[key]:
+                        stalls[0] += 1
+                    while not free[key]:
+                        cv.wait(0.01)
+                    j = free[key].pop()
+                    slot_of[tag0 + i] = (key, j)
+                    meta[tag0 + i] = (shape, c128, inverse)
+                xi, yi = pools[key][j]
+                fftu.fftu_server_submit(server, shape, fftu.FFTU_C128 if c128 else fftu.FFTU_C64,
+                                        fftu.FFTU_INVERSE if inverse else fftu.FFTU_FORWARD, xi.data_ptr(),
+                                        yi.data_ptr(), tag0 + i)
+
+        gen = threading.Thread(target=generator)
+        gen.start()
+        while len(done) < len(kinds):
+            got = fftu.fftu_server_poll(server, 4096)
+            if got:
+                with cv:
+                    for c in got:
+                        key, j = slot_of.pop(c["tag"])
+                        free[key].append(j)
+                    cv.notify_all()
+                done.extend(got)
+            else:
+                time.sleep(2e-4)
+        gen.join()
+        return done, meta, stalls[0]
+
+    # saturation: a closed-loop burst of the same mix (as many in flight as the buffer pools allow)
+    sat_done, _, _ = phase(draw(args.serve_warmup + 2000), None, 0)
+    sat = sorted(sat_done, key=lambda c: c["done_s"])[args.serve_warmup:]
+    sat_rate = (len(sat) - 1) / (sat[-1]["done_s"] - sat[0]["done_s"])
+    rate = args.serve_rate if args.serve_rate > 0 else 0.7 * sat_rate
+    total = args.serve_warmup + args.serve_requests
+    kinds = draw(total)
+    gaps = rng.exponential(1.0 / rate, size=total)
+    stats0 = fftu.fftu_server_stats_get(server)
     wall0 = time.perf_counter()
-    gen.start()
-    stats0 = None
-    while len(done) < total:
-        got = fftu.fftu_server_poll(server, 4096)
-        if got:
-            with cv:
-                for c in got:
-                    key, j = slot_of.pop(c["tag"])
-                    free[key].append(j)
-                cv.notify_all()
-            done.extend(got)
-            if stats0 is None and len(done) >= args.serve_warmup:
-                stats0 = fftu.fftu_server_stats_get(server)
-        else:
-            time.sleep(2e-4)
-    gen.join()
+    done, meta, stalls = phase(kinds, gaps, 10 ** 6)
     wall = time.perf_counter() - wall0
     stats1 = fftu.fftu_server_stats_get(server)
-    timed = [c for c in done if c["tag"] >= args.serve_warmup]
-    bad = [c for c in done if c["status"] != 0]
+    timed = [c for c in done if c["tag"] >= 10 ** 6 + args.serve_warmup]
+    bad = [c for c in done + sat_done if c["status"] != 0]
     lat = np.array([c["done_s"] - c["submit_s"] for c in timed]) * 1e3
     t_first = min(c["submit_s"] for c in timed)
     t_last = max(c["done_s"] for c in timed)
     span = t_last - t_first
     alg = sum(4 * math.prod(meta[c["tag"]][0]) * (16 if meta[c["tag"]][1] else 8) for c in timed)
     moved = sum(2 * math.prod(meta[c["tag"]][0]) * (16 if meta[c["tag"]][1] else 8) for c in timed)
-    d = {k: stats1[k] - (stats0 or {}).get(k, 0) for k in ("batches", "graph_replays", "direct_launches",
-                                                           "kernel_launches", "rejected", "evictions")}
+    d = {k: stats1[k] - stats0[k] for k in ("batches", "graph_replays", "direct_launches", "kernel_launches",
+                                              "rejected", "evictions")}
     per_class = {}
     for shape in SERVE_SHAPES:
         for c128 in (False, True):
@@ -531,16 +583,19 @@ def run_serving(fftu, args, local):
                                       torch.linalg.vector_norm(ref)).item()))
     fftu.fftu_server_destroy(server)
     return {
-        "requests": len(timed), "warmup_requests": args.serve_warmup, "offered_rate_per_s": args.serve_rate,
+        "requests": len(timed), "warmup_requests": args.serve_warmup,
+        "saturation_rate_per_s": sat_rate, "offered_rate_per_s": rate,
+        "offered_fraction_of_saturation": rate / sat_rate,
         "achieved_rate_per_s": len(timed) / span, "p50_ms": float(np.percentile(lat, 50)),
         "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
         "gbs_algorithmic": alg / span / 1e9, "gbs_host_copies": moved / span / 1e9,
-        "failed": len(bad), "pool_stalls": stalls[0], "wall_s": wall, "pinned_pool_alloc_s": t_alloc,
+        "failed": len(bad), "pool_stalls": stalls, "wall_s": wall, "pinned_pool_alloc_s": t_alloc,
         "served_vs_direct_max_rel_l2": worst, **d, "per_class": per_class,
         "server": {"streams": args.serve_streams, "max_inflight": args.serve_inflight or 2 * args.serve_streams,
                    "max_batch": 64, "copy_piece_mib": args.serve_piece_mib},
         "mix": "shapes uniform over 32^3, 64^3, 128^3, 256^3, 1024^2, 2048^2, 4096^2; complex128 w.p. 0.1; "
-               "forward/inverse equiprobable; Poisson arrivals; latency = server completion - submission",
+               "forward/inverse equiprobable; Poisson arrivals at the offered rate (0.7 x the closed-loop "
+               "saturation rate unless --serve-rate is given); latency = server completion - submission",
     }
 
 
@@ -564,10 +619,13 @@ def run_serve_only(args):
         sys.exit(1)
 
 
-def uneven_shapes(count, seed):
-    """Each n_l drawn independently from {32, 64, 128}: sizes 32^3 to 128^3, cubes included."""
+def uneven_shapes(count, seed, cubes=False):
+    """Each n_l drawn independently from {32, 64, 128}: sizes 32^3 to 128^3, cubes included.
+    cubes=True: the other reading, cubes n^3 with n drawn from {32, 64, 128}."""
     import numpy as np
     rng = np.random.default_rng(seed)
+    if cubes:
+        return [(n, n, n) for n in (int(v) for v in rng.choice([32, 64, 128], size=count))]
     return [tuple(int(v) for v in rng.choice([32, 64, 128], size=3)) for _ in range(count)]
 
 
@@ -587,7 +645,7 @@ def run_batch(args):
     import paper_2203_11795_gb300 as fftu
     from fftu_inputs import complex_uniform
 
-    shapes = uneven_shapes(args.batch, args.seed)
+    shapes = uneven_shapes(args.batch, args.seed, cubes=args.batch_cubes)
     hosts = [torch.from_numpy(complex_uniform(args.seed + 1000 * rank + i, s, dtype=np.complex64)).pin_memory()
              for i, s in enumerate(shapes)]
     xs = [h.to(dev) for h in hosts]
@@ -682,8 +740,10 @@ def run_batch(args):
             "value": whole_job_value(step_bytes, ms, world), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batch of {args.batch} uneven complex64 3D transforms (n_l in 32, 64, 128), "
-                                   f"forward+inverse, one persistent launch per direction",
+            "config": {"workload": f"batch of {args.batch} uneven complex64 3D transforms "
+                                   + ("(cubes n^3, n in 32, 64, 128), " if args.batch_cubes else
+                                      "(n_l in 32, 64, 128), ")
+                                   + "forward+inverse, one persistent launch per direction",
                        "elements": elems, "bytes_per_array_set": elems * 8,
                        "l2": "arrays total more than L2 but part of a step's working set stays L2-resident",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
