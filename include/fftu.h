@@ -90,11 +90,28 @@ typedef enum {
  * bfloat16, 2^-11 for float16), against about 2^-24 for FP32. */
 typedef enum { FFTU_PREC_NATIVE = 0, FFTU_PREC_SPLIT_BF16 = 1, FFTU_PREC_SPLIT_FP16 = 2 } fftu_precision;
 
+/* Storage of `in` and `out`.  NATURAL: the global row-major array; the cyclic distribution of Sec. 1.1
+ * is a view of it (element j belongs to processor s = j mod p at local index j div p, per axis).
+ * CYCLIC: the processors' local arrays X^{(s)} (each row-major over n/p) concatenated in row-major
+ * order of s, i.e. what each of the paper's processors holds.  Input and output use the same layout
+ * (Algorithm 2.3 keeps the distribution).  CYCLIC costs two extra HBM round trips (three in place):
+ * the transform runs on the natural view between two permutation passes.  Phase A alone then
+ * writes W in CYCLIC layout (W^{(k)} concatenated) and phase B alone reads and writes it. */
+typedef enum { FFTU_LAYOUT_NATURAL = 0, FFTU_LAYOUT_CYCLIC = 1 } fftu_layout;
+
+/* Who provides the plan's device workspace (fftu_workspace_size bytes; may be 0).
+ * PLAN: the plan allocates it at plan time and frees it in fftu_destroy.
+ * CALLER: the plan allocates none; fftu_exec* returns FFTU_ERR_ARG until fftu_set_workspace
+ * supplies one (e.g. from the caller's own allocator). */
+typedef enum { FFTU_WORKSPACE_PLAN = 0, FFTU_WORKSPACE_CALLER = 1 } fftu_workspace_mode;
+
 typedef struct {
     int schedule;        /* fftu_schedule */
     int tune;            /* with p == NULL: time candidate grids at plan time and keep the fastest */
     int precision;       /* fftu_precision */
-    int reserved[5];     /* must be zero */
+    int layout;          /* fftu_layout */
+    int workspace_mode;  /* fftu_workspace_mode */
+    int reserved[3];     /* must be zero */
 } fftu_options;
 
 typedef struct {
@@ -112,6 +129,9 @@ typedef struct {
     int64_t workspace_bytes;   /* device bytes of workspace owned by the plan */
     int tuned;                 /* 1 when p was chosen by measurement (fftu_options.tune) */
     int precision;             /* fftu_precision of the radix-16 stages */
+    int64_t workspace_need;    /* device bytes of workspace the plan uses (owned or supplied) */
+    int layout;                /* fftu_layout */
+    int workspace_mode;        /* fftu_workspace_mode */
 } fftu_info;
 
 /*
@@ -243,6 +263,17 @@ fftu_status fftu_batch_destroy(fftu_batch batch);
 fftu_status fftu_wisdom_export(const char *path);
 fftu_status fftu_wisdom_import(const char *path);
 fftu_status fftu_wisdom_forget(void);
+
+/* Bytes of device workspace the plan needs (0 for plans that need none).  Synchronous, host only. */
+fftu_status fftu_workspace_size(fftu_handle plan, size_t *bytes);
+
+/* Make the plan use `workspace` (device memory of at least fftu_workspace_size bytes, 256-byte
+ * aligned, owned by the caller and kept alive until every exec that used it has completed) instead
+ * of its own; a workspace the plan allocated itself is freed first (after a device synchronisation).
+ * workspace == NULL detaches it (execs then fail with FFTU_ERR_ARG until another is set).  Execs of
+ * one plan that overlap on the GPU must use different workspaces: give each stream its own plan, or
+ * set a stream's workspace before its exec and order them. */
+fftu_status fftu_set_workspace(fftu_handle plan, void *workspace, size_t bytes);
 
 /* Static string for a status code. */
 const char *fftu_status_string(fftu_status s);

@@ -24,6 +24,8 @@ FFTU_FORWARD, FFTU_INVERSE = -1, 1
 FFTU_PHASE_A, FFTU_PHASE_B, FFTU_PHASE_ALL = 1, 2, 3
 FFTU_SCHED_AUTO, FFTU_SCHED_GENERIC, FFTU_SCHED_FUSED, FFTU_SCHED_GENERIC_A = 0, 1, 2, 3
 FFTU_PREC_NATIVE, FFTU_PREC_SPLIT_BF16, FFTU_PREC_SPLIT_FP16 = 0, 1, 2
+FFTU_LAYOUT_NATURAL, FFTU_LAYOUT_CYCLIC = 0, 1
+FFTU_WORKSPACE_PLAN, FFTU_WORKSPACE_CALLER = 0, 1
 STATUS_NAMES = {0: "FFTU_OK", 1: "FFTU_ERR_ARG", 2: "FFTU_ERR_DIVISIBILITY", 3: "FFTU_ERR_UNSUPPORTED",
                 4: "FFTU_ERR_NOMEM", 5: "FFTU_ERR_CUDA", 6: "FFTU_ERR_TIMEOUT", 7: "FFTU_ERR_INTERNAL"}
 
@@ -32,7 +34,8 @@ EXPORTS = ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_ex
            "fftu_plan_info",
            "fftu_check_device_status", "fftu_exec_noalloc", "fftu_batch_create", "fftu_batch_exec",
            "fftu_batch_check_status", "fftu_batch_destroy", "fftu_wisdom_export", "fftu_wisdom_import",
-           "fftu_wisdom_forget", "fftu_status_string", "fftu_last_error", "fftu_version",
+           "fftu_wisdom_forget", "fftu_workspace_size", "fftu_set_workspace", "fftu_status_string",
+           "fftu_last_error", "fftu_version",
            # include/fftu_serve.h
            "fftu_server_create", "fftu_server_submit", "fftu_server_poll", "fftu_server_drain",
            "fftu_server_stats_get", "fftu_server_destroy")
@@ -47,7 +50,7 @@ class FFTUError(RuntimeError):
 
 class fftu_options(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int), ("tune", ctypes.c_int), ("precision", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("layout", ctypes.c_int), ("workspace_mode", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class fftu_info(ctypes.Structure):
@@ -55,7 +58,8 @@ class fftu_info(ctypes.Structure):
                 ("dtype", ctypes.c_int), ("dir", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("launches_phase_a", ctypes.c_int), ("launches_phase_b", ctypes.c_int),
                 ("N", ctypes.c_int64), ("alg_bytes", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
-                ("workspace_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("workspace_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("precision", ctypes.c_int),
+                ("workspace_need", ctypes.c_int64), ("layout", ctypes.c_int), ("workspace_mode", ctypes.c_int)]
 
 
 class fftu_server_config(ctypes.Structure):
@@ -106,6 +110,8 @@ def _load_library() -> ctypes.CDLL:
     lib.fftu_wisdom_export.argtypes = [ctypes.c_char_p]
     lib.fftu_wisdom_import.argtypes = [ctypes.c_char_p]
     lib.fftu_wisdom_forget.argtypes = []
+    lib.fftu_workspace_size.argtypes = [h, ctypes.POINTER(ctypes.c_size_t)]
+    lib.fftu_set_workspace.argtypes = [h, vp, ctypes.c_size_t]
     lib.fftu_server_create.argtypes = [ctypes.POINTER(fftu_server_config), ctypes.POINTER(h)]
     lib.fftu_server_submit.argtypes = [h, ctypes.POINTER(fftu_request)]
     lib.fftu_server_poll.argtypes = [h, ctypes.POINTER(fftu_completion), ctypes.c_int]
@@ -119,7 +125,8 @@ def _load_library() -> ctypes.CDLL:
     for name in ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_exec_pointwise", "fftu_destroy",
                  "fftu_plan_info", "fftu_check_device_status", "fftu_exec_noalloc", "fftu_batch_create",
                  "fftu_batch_exec", "fftu_batch_check_status", "fftu_batch_destroy", "fftu_wisdom_export",
-                 "fftu_wisdom_import", "fftu_wisdom_forget", "fftu_server_create", "fftu_server_submit",
+                 "fftu_wisdom_import", "fftu_wisdom_forget", "fftu_workspace_size", "fftu_set_workspace",
+                 "fftu_server_create", "fftu_server_submit",
                  "fftu_server_poll", "fftu_server_drain", "fftu_server_stats_get", "fftu_server_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
@@ -161,9 +168,11 @@ def fftu_plan(d: int, n, p, dtype: int, direction: int) -> int:
 
 
 def fftu_plan_ex(d: int, n, p, dtype: int, direction: int, schedule: int = FFTU_SCHED_AUTO,
-                 tune: bool = False, precision: int = FFTU_PREC_NATIVE) -> int:
+                 tune: bool = False, precision: int = FFTU_PREC_NATIVE, layout: int = FFTU_LAYOUT_NATURAL,
+                 workspace_mode: int = FFTU_WORKSPACE_PLAN) -> int:
     h = ctypes.c_void_p()
-    opts = fftu_options(schedule=int(schedule), tune=int(bool(tune)), precision=int(precision))
+    opts = fftu_options(schedule=int(schedule), tune=int(bool(tune)), precision=int(precision), layout=int(layout),
+                        workspace_mode=int(workspace_mode))
     _check(_lib.fftu_plan_ex(int(d), _i64(n), _i64(p), int(dtype), int(direction), ctypes.byref(opts),
                              ctypes.byref(h)), "fftu_plan_ex")
     return h.value
@@ -195,7 +204,8 @@ def fftu_plan_info(plan: int) -> dict:
             "schedule": info.schedule, "launches_phase_a": info.launches_phase_a,
             "launches_phase_b": info.launches_phase_b, "N": info.N, "alg_bytes": info.alg_bytes,
             "table_bytes": info.table_bytes, "workspace_bytes": info.workspace_bytes, "tuned": info.tuned,
-            "precision": info.precision}
+            "precision": info.precision, "workspace_need": info.workspace_need, "layout": info.layout,
+            "workspace_mode": info.workspace_mode}
 
 
 def fftu_check_device_status(plan: int) -> None:
@@ -283,6 +293,16 @@ def fftu_server_destroy(server: int) -> None:
     _check(_lib.fftu_server_destroy(server), "fftu_server_destroy")
 
 
+def fftu_workspace_size(plan: int) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib.fftu_workspace_size(plan, ctypes.byref(b)), "fftu_workspace_size")
+    return int(b.value)
+
+
+def fftu_set_workspace(plan: int, ptr, nbytes: int) -> None:
+    _check(_lib.fftu_set_workspace(plan, ptr, int(nbytes)), "fftu_set_workspace")
+
+
 def fftu_status_string(status: int) -> str:
     return _lib.fftu_status_string(int(status)).decode()
 
@@ -310,15 +330,16 @@ class Plan:
     """A plan for one shape, cyclic grid p, dtype and direction (fftu_plan)."""
 
     def __init__(self, n, p=None, dtype=None, inverse: bool = False, schedule: int = FFTU_SCHED_AUTO,
-                 tune: bool = False, precision: int = FFTU_PREC_NATIVE):
+                 tune: bool = False, precision: int = FFTU_PREC_NATIVE, layout: int = FFTU_LAYOUT_NATURAL,
+                 workspace_mode: int = FFTU_WORKSPACE_PLAN):
         import torch
         self.n = tuple(int(v) for v in n)
         self.dtype = dtype if dtype is not None else torch.complex64
         code = _dtype_code(self.dtype)
         self.inverse = bool(inverse)
         self.handle = fftu_plan_ex(len(self.n), self.n, None if p is None else list(p), code,
-                                   FFTU_INVERSE if inverse else FFTU_FORWARD, schedule, tune, precision)
-        self.info = fftu_plan_info(self.handle)
+                                   FFTU_INVERSE if inverse else FFTU_FORWARD, schedule, tune, precision, layout,
+                                   workspace_mode)
         self.p = tuple(self.info["p"])
 
     def _validate(self, t, name):
@@ -347,6 +368,11 @@ class Plan:
         s = stream if stream is not None else torch.cuda.current_stream(out.device)
         fftu_exec_phase(self.handle, phase, None if x is None else x.data_ptr(), out.data_ptr(), s.cuda_stream)
         return out
+
+    @property
+    def info(self) -> dict:
+        """fftu_plan_info, read now (workspace fields change with fftu_set_workspace)."""
+        return fftu_plan_info(self.handle)
 
     def check_device_status(self):
         fftu_check_device_status(self.handle)

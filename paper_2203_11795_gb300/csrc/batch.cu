@@ -198,6 +198,10 @@ fftu_status batch_create(int count, const fftu_handle *plans, Batch **out_batch)
             record_error("batch: every plan needs the same dtype, direction and device");
             return FFTU_ERR_ARG;
         }
+        if (views[i].layout != 0) {
+            record_error("batch: CYCLIC-layout plans are not batched");
+            return FFTU_ERR_UNSUPPORTED;
+        }
         if (views[i].precision != 0) {
             record_error("batch: split-precision plans are not batched");
             return FFTU_ERR_UNSUPPORTED;

@@ -108,8 +108,14 @@ struct Plan {
     void *tables = nullptr;
     size_t table_bytes = 0;
     int64_t table_off[FFTU_MAX_DIMS] = {};
-    void *workspace = nullptr;
-    size_t workspace_bytes = 0;
+    void *workspace = nullptr;   // [natural schedule's part | CYCLIC layout temp], plan-owned or caller's
+    size_t workspace_bytes = 0;  // bytes the plan allocated itself (0 when the caller supplies it)
+    bool ws_owned = false;
+    size_t ws_natural = 0;       // bytes the natural schedule needs (ring or two-kernel scratch, ping-pong)
+    size_t ws_need = 0;          // total: natural part rounded to 256 B, plus N elements for CYCLIC
+    size_t ring_counter_off = 0; // ring schedule: offset of its counters in the workspace
+    int layout = 0;              // fftu_layout
+    int workspace_mode = 0;      // fftu_workspace_mode
     int *dstatus = nullptr;
     int tuned = 0;
     std::vector<Step> phase_a, phase_b;
@@ -286,17 +292,8 @@ fftu_status build_fused_phase_a(Plan &pl, bool *used) {
         l.ring = 0;
         ws = (size_t)pl.N * pl.esize;
     }
-    e = cudaMalloc(&pl.workspace, ws);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        set_err("cudaMalloc of %zu workspace bytes: %s", ws, cudaGetErrorString(e));
-        return FFTU_ERR_NOMEM;
-    }
-    pl.workspace_bytes = ws;
-    l.scratch = pl.workspace;
-    if (l.mode == 1)
-        l.counters = reinterpret_cast<unsigned *>(static_cast<char *>(pl.workspace) +
-                                                  ((size_t)kRingSlots * unit_bytes + 255) / 256 * 256);
+    pl.ws_natural = ws;  // scratch and counters are bound to the workspace once it exists
+    if (l.mode == 1) pl.ring_counter_off = ((size_t)kRingSlots * unit_bytes + 255) / 256 * 256;
     pl.phase_a.push_back(s);
     *used = true;
     return FFTU_OK;
@@ -317,16 +314,7 @@ fftu_status build_schedule(Plan &pl, int sched) {
         // a pass over part of the classes of a line is not in place: alternate with a workspace
         for (const Step &s : pl.phase_a)
             if (s.kind == STEP_AXIS && s.axis.Gt < s.axis.G) pl.generic_pingpong = true;
-        if (pl.generic_pingpong) {
-            const size_t ws = (size_t)pl.N * pl.esize;
-            cudaError_t e = cudaMalloc(&pl.workspace, ws);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                set_err("cudaMalloc of %zu workspace bytes: %s", ws, cudaGetErrorString(e));
-                return FFTU_ERR_NOMEM;
-            }
-            pl.workspace_bytes = ws;
-        }
+        if (pl.generic_pingpong) pl.ws_natural = (size_t)pl.N * pl.esize;
     }
     // Phase B: one fused pass when every p_l <= 16, else one pass per axis.
     Step s;
@@ -369,10 +357,25 @@ int kernel_count(const std::vector<Step> &steps) {
     return k;
 }
 
+// Point the steps that use the workspace at pl->workspace (NULL when the caller has not supplied one).
+void bind_workspace(Plan *pl) {
+    for (Step &s : pl->phase_a)
+        if (s.kind == STEP_PHASE_A3) {
+            s.a3.scratch = pl->workspace;
+            s.a3.counters = pl->workspace && s.a3.mode == 1
+                                ? reinterpret_cast<unsigned *>(static_cast<char *>(pl->workspace) + pl->ring_counter_off)
+                                : nullptr;
+        }
+}
+
+void *layout_temp(const Plan *pl) {
+    return static_cast<char *>(pl->workspace) + (pl->ws_natural + 255) / 256 * 256;
+}
+
 void free_plan(Plan *pl) {
     if (!pl) return;
     if (pl->tables) cudaFree(pl->tables);
-    if (pl->workspace) cudaFree(pl->workspace);
+    if (pl->workspace && pl->ws_owned) cudaFree(pl->workspace);
     if (pl->dstatus) cudaFree(pl->dstatus);
     delete pl;
 }
@@ -441,6 +444,7 @@ fftu_status plan_view(fftu_handle h, PlanView *v) {
     v->device = pl.device;
     v->pingpong = pl.generic_pingpong;
     v->precision = pl.precision;
+    v->layout = pl.layout;
     v->a_passes.clear();
     v->b_steps.clear();
     const bool fused_a = !pl.phase_a.empty() && pl.phase_a[0].kind == STEP_PHASE_A3;
@@ -503,6 +507,16 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
     const int precision = opts ? opts->precision : FFTU_PREC_NATIVE;
     if (precision < FFTU_PREC_NATIVE || precision > FFTU_PREC_SPLIT_FP16) {
         set_err("unknown precision %d", precision);
+        return FFTU_ERR_ARG;
+    }
+    const int layout = opts ? opts->layout : FFTU_LAYOUT_NATURAL;
+    const int ws_mode = opts ? opts->workspace_mode : FFTU_WORKSPACE_PLAN;
+    if (layout != FFTU_LAYOUT_NATURAL && layout != FFTU_LAYOUT_CYCLIC) {
+        set_err("unknown layout %d", layout);
+        return FFTU_ERR_ARG;
+    }
+    if (ws_mode != FFTU_WORKSPACE_PLAN && ws_mode != FFTU_WORKSPACE_CALLER) {
+        set_err("unknown workspace mode %d", ws_mode);
         return FFTU_ERR_ARG;
     }
     if (precision != FFTU_PREC_NATIVE) {
@@ -581,6 +595,8 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
     pl->dir = dir;
     pl->tuned = tuned;
     pl->precision = precision;
+    pl->layout = layout;
+    pl->workspace_mode = ws_mode;
     pl->N = N;
     pl->esize = dtype == FFTU_C128 ? 16 : 8;
     cudaError_t e = cudaGetDevice(&pl->device);
@@ -636,6 +652,23 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
         free_plan(pl);
         return st;
     }
+    // one workspace: the natural schedule's part, then N elements for the CYCLIC permutations
+    pl->ws_need = pl->ws_natural == 0 && layout == FFTU_LAYOUT_NATURAL
+                      ? 0
+                      : (pl->ws_natural + 255) / 256 * 256 +
+                            (layout == FFTU_LAYOUT_CYCLIC ? (size_t)pl->N * pl->esize : 0);
+    if (pl->ws_need > 0 && ws_mode == FFTU_WORKSPACE_PLAN) {
+        e = cudaMalloc(&pl->workspace, pl->ws_need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_err("cudaMalloc of %zu workspace bytes: %s", pl->ws_need, cudaGetErrorString(e));
+            free_plan(pl);
+            return FFTU_ERR_NOMEM;
+        }
+        pl->ws_owned = true;
+        pl->workspace_bytes = pl->ws_need;
+    }
+    bind_workspace(pl);
     fftu_plan_st *h = new (std::nothrow) fftu_plan_st;
     if (!h) {
         free_plan(pl);
@@ -652,38 +685,13 @@ fftu_status fftu_plan(int d, const int64_t *n, const int64_t *p, fftu_dtype dtyp
     return fftu_plan_ex(d, n, p, dtype, dir, nullptr, out);
 }
 
-fftu_status fftu_exec_phase(fftu_handle h, fftu_phase phase, const void *in, void *out, void *stream) {
-    using namespace fftu;
-    g_err[0] = '\0';
-    if (!h || !h->impl) {
-        set_err("plan is NULL");
-        return FFTU_ERR_ARG;
-    }
-    Plan *pl = h->impl;
-    if (phase != FFTU_PHASE_A && phase != FFTU_PHASE_B && phase != FFTU_PHASE_ALL) {
-        set_err("unknown phase %d", (int)phase);
-        return FFTU_ERR_ARG;
-    }
-    if (!out || ((phase & FFTU_PHASE_A) && !in)) {
-        set_err("in/out must be non-NULL device pointers");
-        return FFTU_ERR_ARG;
-    }
-    if (phase == FFTU_PHASE_B && in && in != out) {
-        set_err("phase B runs in place: in must be NULL or equal to out");
-        return FFTU_ERR_ARG;
-    }
-    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) {
-        set_err("in/out must be 16-byte aligned");
-        return FFTU_ERR_ARG;
-    }
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev != pl->device) {
-        set_err("plan was made on device %d, current device is %d", pl->device, dev);
-        return FFTU_ERR_ARG;
-    }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace fftu {
+namespace {
+
+// The transform on the natural view (every layout ends up here).
+fftu_status exec_natural(Plan *pl, fftu_phase phase, const void *in, void *out, cudaStream_t st) {
     if ((phase & FFTU_PHASE_A) && pl->generic_pingpong) {
         // buffers: pass k (of d) writes out when d - k is even, the workspace otherwise
         const int np = (int)pl->phase_a.size();
@@ -718,6 +726,82 @@ fftu_status fftu_exec_phase(fftu_handle h, fftu_phase phase, const void *in, voi
     return FFTU_OK;
 }
 
+// CYCLIC layout: permute to the natural view, run it, permute back (see fftu_layout).
+fftu_status exec_cyclic(Plan *pl, fftu_phase phase, const void *in, void *out, cudaStream_t st) {
+    const int dbl = pl->dtype == FFTU_C128;
+    const size_t bytes = (size_t)pl->N * pl->esize;
+    void *tmp = layout_temp(pl);
+    cudaError_t e;
+    if (!(phase & FFTU_PHASE_A)) {  // phase B alone, in place on out
+        e = launch_cyclic_permute(out, tmp, pl->d, pl->n, pl->p, dbl, 0, st);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        fftu_status s = exec_natural(pl, phase, tmp, tmp, st);
+        if (s != FFTU_OK) return s;
+        e = launch_cyclic_permute(tmp, out, pl->d, pl->n, pl->p, dbl, 1, st);
+        return e == cudaSuccess ? FFTU_OK : cuda_fail(e, "kernel launch");
+    }
+    if (in != out) {  // natural input in out, natural result in tmp, back to CYCLIC in out
+        e = launch_cyclic_permute(in, out, pl->d, pl->n, pl->p, dbl, 0, st);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        fftu_status s = exec_natural(pl, phase, out, tmp, st);
+        if (s != FFTU_OK) return s;
+        e = launch_cyclic_permute(tmp, out, pl->d, pl->n, pl->p, dbl, 1, st);
+        return e == cudaSuccess ? FFTU_OK : cuda_fail(e, "kernel launch");
+    }
+    // in place: natural input in tmp, natural result in out, CYCLIC result in tmp, copied to out
+    e = launch_cyclic_permute(in, tmp, pl->d, pl->n, pl->p, dbl, 0, st);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    fftu_status s = exec_natural(pl, phase, tmp, out, st);
+    if (s != FFTU_OK) return s;
+    e = launch_cyclic_permute(out, tmp, pl->d, pl->n, pl->p, dbl, 1, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? FFTU_OK : cuda_fail(e, "kernel launch");
+}
+
+}  // namespace
+}  // namespace fftu
+
+extern "C" {
+
+fftu_status fftu_exec_phase(fftu_handle h, fftu_phase phase, const void *in, void *out, void *stream) {
+    using namespace fftu;
+    g_err[0] = '\0';
+    if (!h || !h->impl) {
+        set_err("plan is NULL");
+        return FFTU_ERR_ARG;
+    }
+    Plan *pl = h->impl;
+    if (phase != FFTU_PHASE_A && phase != FFTU_PHASE_B && phase != FFTU_PHASE_ALL) {
+        set_err("unknown phase %d", (int)phase);
+        return FFTU_ERR_ARG;
+    }
+    if (!out || ((phase & FFTU_PHASE_A) && !in)) {
+        set_err("in/out must be non-NULL device pointers");
+        return FFTU_ERR_ARG;
+    }
+    if (phase == FFTU_PHASE_B && in && in != out) {
+        set_err("phase B runs in place: in must be NULL or equal to out");
+        return FFTU_ERR_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) {
+        set_err("in/out must be 16-byte aligned");
+        return FFTU_ERR_ARG;
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != pl->device) {
+        set_err("plan was made on device %d, current device is %d", pl->device, dev);
+        return FFTU_ERR_ARG;
+    }
+    if (pl->ws_need > 0 && !pl->workspace) {
+        set_err("the plan has no workspace: supply one with fftu_set_workspace");
+        return FFTU_ERR_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return pl->layout == FFTU_LAYOUT_CYCLIC ? exec_cyclic(pl, phase, in, out, st) : exec_natural(pl, phase, in, out, st);
+}
+
 fftu_status fftu_exec(fftu_handle h, const void *in, void *out, void *stream) {
     return fftu_exec_phase(h, FFTU_PHASE_ALL, in, out, stream);
 }
@@ -739,6 +823,14 @@ fftu_status fftu_exec_pointwise(fftu_handle fwd, fftu_handle inv, const void *in
     for (int l = 0; same && l < pf->d; ++l) same = pf->n[l] == pi->n[l] && pf->p[l] == pi->p[l];
     if (!same) {
         set_err("fwd and inv must have the same shape, cyclic grid, dtype and device");
+        return FFTU_ERR_ARG;
+    }
+    if (pf->layout != FFTU_LAYOUT_NATURAL || pi->layout != FFTU_LAYOUT_NATURAL) {
+        set_err("fftu_exec_pointwise takes NATURAL-layout plans");
+        return FFTU_ERR_UNSUPPORTED;
+    }
+    if ((pf->ws_need > 0 && !pf->workspace) || (pi->ws_need > 0 && !pi->workspace)) {
+        set_err("a plan has no workspace: supply one with fftu_set_workspace");
         return FFTU_ERR_ARG;
     }
     if (!in || !mul || !tmp || !out || tmp == out || mul == tmp) {
@@ -818,6 +910,43 @@ fftu_status fftu_plan_info(fftu_handle h, fftu_info *info) {
     info->workspace_bytes = (int64_t)pl->workspace_bytes;
     info->tuned = pl->tuned;
     info->precision = pl->precision;
+    info->workspace_need = (int64_t)pl->ws_need;
+    info->layout = pl->layout;
+    info->workspace_mode = pl->workspace_mode;
+    return FFTU_OK;
+}
+
+fftu_status fftu_workspace_size(fftu_handle h, size_t *bytes) {
+    using namespace fftu;
+    if (!h || !h->impl || !bytes) {
+        set_err("plan and bytes must be non-NULL");
+        return FFTU_ERR_ARG;
+    }
+    *bytes = h->impl->ws_need;
+    return FFTU_OK;
+}
+
+fftu_status fftu_set_workspace(fftu_handle h, void *workspace, size_t bytes) {
+    using namespace fftu;
+    g_err[0] = '\0';
+    if (!h || !h->impl) {
+        set_err("plan is NULL");
+        return FFTU_ERR_ARG;
+    }
+    Plan *pl = h->impl;
+    if (workspace && (bytes < pl->ws_need || (reinterpret_cast<uintptr_t>(workspace) & 255))) {
+        set_err("workspace must hold %zu bytes and be 256-byte aligned", pl->ws_need);
+        return FFTU_ERR_ARG;
+    }
+    if (pl->ws_owned && pl->workspace) {
+        cudaError_t e = cudaDeviceSynchronize();  // execs in flight may still use it
+        if (e != cudaSuccess) return cuda_fail(e, "synchronize before freeing the workspace");
+        cudaFree(pl->workspace);
+    }
+    pl->workspace = workspace;
+    pl->ws_owned = false;
+    pl->workspace_bytes = 0;
+    bind_workspace(pl);
     return FFTU_OK;
 }
 

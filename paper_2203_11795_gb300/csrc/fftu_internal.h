@@ -100,10 +100,16 @@ struct PlanView {
     int dtype, dir, device;
     bool pingpong;                  // phase A alternates with a workspace (long lines)
     int precision;                  // fftu_precision of the plan's radix-16 stages
+    int layout;                     // fftu_layout
     std::vector<StepView> a_passes;  // phase A, generic passes (first reads in, then in place on out)
     std::vector<StepView> b_steps;   // phase B, in place on out
 };
 fftu_status plan_view(fftu_handle h, PlanView *v);
+
+// Move an array between the natural row-major layout and the CYCLIC processor-major layout
+// (layout.cu); to_cyclic = 1: natural -> CYCLIC, 0: CYCLIC -> natural.  src != dst.
+cudaError_t launch_cyclic_permute(const void *src, void *dst, int d, const int64_t *n, const int64_t *p,
+                                  int is_double, int to_cyclic, cudaStream_t st);
 
 // Plan-time tuning of p (tuner.cu); false: use the default grid.
 bool autotune_grid(int d, const int64_t *n, fftu_dtype dtype, fftu_dir dir, int sched, int64_t *p_out);

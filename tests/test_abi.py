@@ -95,3 +95,17 @@ def test_precision_option_validation():
     with pytest.raises(f.FFTUError) as ei:
         f.fftu_plan_ex(3, [64, 64, 64], None, f.FFTU_C64, f.FFTU_FORWARD, schedule=9)
     assert ei.value.status == 1
+
+
+def test_layout_and_workspace_validation():
+    """Unknown layouts and workspace modes are refused before any device work; the workspace
+    entry points reject NULL plans."""
+    import paper_2203_11795_gb300 as f
+    for kw in ({"layout": 5}, {"workspace_mode": 3}):
+        with pytest.raises(f.FFTUError) as ei:
+            f.fftu_plan_ex(3, [64, 64, 64], None, f.FFTU_C64, f.FFTU_FORWARD, **kw)
+        assert ei.value.status == 1
+    with pytest.raises(f.FFTUError):
+        f.fftu_workspace_size(None)
+    with pytest.raises(f.FFTUError):
+        f.fftu_set_workspace(None, None, 0)
