@@ -64,6 +64,9 @@ def parse_args():
                     help="radix-16 stages on CUDA cores (native) or as split bf16/fp16 tensor-core contractions")
     ap.add_argument("--inputs", choices=["uniform", "loguniform"], default="uniform")
     ap.add_argument("--seed", type=int, default=2024)
+    ap.add_argument("--flush-l2", action="store_true",
+                    help="write a 256 MB buffer between steps (for arrays that fit in L2); the step time is "
+                         "then the sum of the phases' event intervals, the flush excluded")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -262,7 +265,11 @@ def run_ours(args):
     sh = stream.cuda_stream
     A, B = fftu.FFTU_PHASE_A, fftu.FFTU_PHASE_B
 
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev) if args.flush_l2 else None
+
     def step(ev=None):
+        if flush is not None:
+            flush.zero_()
         if ev is not None:
             ev[0].record(stream)
         fftu.fftu_exec_phase(fwd.handle, A, x.data_ptr(), y.data_ptr(), sh)
@@ -301,6 +308,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     total_ms = t_start.elapsed_time(t_end)
+    if flush is not None:  # the flushes are not part of the step
+        total_ms = sum(ev[0].elapsed_time(ev[4]) for ev in events)
     phase_a = [ev[0].elapsed_time(ev[1]) for ev in events] + [ev[2].elapsed_time(ev[3]) for ev in events]
     phase_b = [ev[1].elapsed_time(ev[2]) for ev in events] + [ev[3].elapsed_time(ev[4]) for ev in events]
     total_ms = max_over_ranks(total_ms, dev)
@@ -422,8 +431,11 @@ def run_ours(args):
                        "shape": list(shape), "p": list(p), "schedule": fwd.info["schedule"],
                        "precision": args.precision, "inputs": args.inputs,
                        "p_inverse": inv.info["p"], "tuned": tune, "plan_seconds": t_plan,
-                       "l2": ("inputs larger than L2 (129 MB); no flush" if N * esize > 129e6 else
+                       "l2": ("L2 flushed between steps (256 MB written); step time = sum of phase events"
+                              if args.flush_l2 else
+                              "inputs larger than L2 (129 MB); no flush" if N * esize > 129e6 else
                               "inputs smaller than L2: L2-resident, not an HBM measurement"),
+                       "seed": args.seed, "inputs_recipe": f"fftu_inputs {args.inputs}, seed + rank",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "gflops_5NlogN": world * 2 * 5 * N * math.log2(N) / (ms_per_step * 1e-3) / 1e9},
             "roofline": roofline,

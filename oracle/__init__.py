@@ -123,6 +123,15 @@ def dft_points(x, ks, inverse: bool = False) -> np.ndarray:
     return y
 
 
+def max_abs_rel(y, y_ref) -> float:
+    """max |y - y_ref| / max |y_ref| over the whole array, in FP64."""
+    y = np.asarray(y, dtype=np.complex128).ravel()
+    r = np.asarray(y_ref, dtype=np.complex128).ravel()
+    den = float(np.abs(r).max()) if r.size else 0.0
+    num = float(np.abs(y - r).max()) if r.size else 0.0
+    return num / den if den > 0 else num
+
+
 def rel_l2(y, y_ref) -> float:
     """||y - y_ref||_2 / ||y_ref||_2 over the whole array, in FP64."""
     y = np.asarray(y, dtype=np.complex128).ravel()

@@ -172,7 +172,11 @@ def test_full_size_512_forward_inverse(fftu, shape, p):
         inv.check_device_status()
     N = x.size
     ref = oracle.fftn(x.astype(np.complex128))
-    assert oracle.rel_l2(y.cpu().numpy(), ref) <= tolerance(np.complex64, N)
+    yh = y.cpu().numpy()
+    err, emax = oracle.rel_l2(yh, ref), oracle.max_abs_rel(yh, ref)
+    print(f"{shape} p={p}: relative L2 {err:.3e}, max-abs / max|ref| {emax:.3e}")
+    assert err <= tolerance(np.complex64, N)
+    assert emax <= tolerance(np.complex64, N)  # the largest outputs carry most of the norm
     del ref
     assert oracle.rel_l2(back.cpu().numpy(), x) <= tolerance(np.complex64, N)
 
@@ -202,7 +206,10 @@ def test_full_size_2d_16384(fftu, p):
     x = complex_uniform(2025, shape, dtype=np.complex64)
     y, _ = run_gpu(fftu, x, p)
     ref = oracle.fftn(x.astype(np.complex128))
-    assert oracle.rel_l2(y, ref) <= tolerance(np.complex64, x.size)
+    err, emax = oracle.rel_l2(y, ref), oracle.max_abs_rel(y, ref)
+    print(f"{shape} p={p}: relative L2 {err:.3e}, max-abs / max|ref| {emax:.3e}")
+    assert err <= tolerance(np.complex64, x.size)
+    assert emax <= tolerance(np.complex64, x.size)
 
 
 @pytest.mark.parametrize("p", [(8, 8, 8), (4, 4, 4)], ids=["p8", "p4"])

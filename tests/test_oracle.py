@@ -150,3 +150,15 @@ def test_pins_catch_planted_mistakes():
     assert oracle.rel_l2(oracle.fftn(good, inverse=True), x) < TOL64
     for name, (arr, expect) in wrong.items():
         assert oracle.rel_l2(arr, expect) > 1e-3, name
+
+
+def test_error_metrics():
+    """rel_l2 and max_abs_rel on hand-checkable arrays."""
+    import oracle
+    ref = np.array([3 + 4j, 0, 0, 0])
+    y = np.array([3 + 4j, 0.5, 0, 0])
+    assert oracle.rel_l2(y, ref) == pytest.approx(0.1)
+    assert oracle.max_abs_rel(y, ref) == pytest.approx(0.1)
+    y = np.array([3 + 4j, 0.3, 0.4j, 0])
+    assert oracle.rel_l2(y, ref) == pytest.approx(0.1)
+    assert oracle.max_abs_rel(y, ref) == pytest.approx(0.08)
