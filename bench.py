@@ -431,6 +431,7 @@ def run_ours(args):
                        "shape": list(shape), "p": list(p), "schedule": fwd.info["schedule"],
                        "precision": args.precision, "inputs": args.inputs,
                        "p_inverse": inv.info["p"], "tuned": tune, "plan_seconds": t_plan,
+                       "strided_tile": fwd.info["tile"], "strided_radix": fwd.info["radix"],
                        "l2": ("L2 flushed between steps (256 MB written); step time = sum of phase events"
                               if args.flush_l2 else
                               "inputs larger than L2 (129 MB); no flush" if N * esize > 129e6 else

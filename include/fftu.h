@@ -111,7 +111,11 @@ typedef struct {
     int precision;       /* fftu_precision */
     int layout;          /* fftu_layout */
     int workspace_mode;  /* fftu_workspace_mode */
-    int reserved[3];     /* must be zero */
+    int tile;            /* strided passes: elements per whole-line tile, a power of two in [1024, 8192]
+                            (complex128: [1024, 4096]); 0 = default (4096 / 2048) */
+    int radix;           /* strided passes' stages: 8 = radix 8 after one smaller first stage (default,
+                            also 0); 16 = radix-16 stages then one stage of the remaining factor */
+    int reserved[1];     /* must be zero */
 } fftu_options;
 
 typedef struct {
@@ -132,6 +136,8 @@ typedef struct {
     int64_t workspace_need;    /* device bytes of workspace the plan uses (owned or supplied) */
     int layout;                /* fftu_layout */
     int workspace_mode;        /* fftu_workspace_mode */
+    int tile;                  /* whole-line tile target of the strided passes (elements) */
+    int radix;                 /* 8 or 16: the strided passes' stage radix */
 } fftu_info;
 
 /*
@@ -154,10 +160,13 @@ fftu_status fftu_plan(int d, const int64_t *n, const int64_t *p, fftu_dtype dtyp
                       fftu_handle *out);
 
 /* fftu_plan with options (opts may be NULL = defaults).  With p == NULL and opts->tune != 0 the
- * planner times every candidate grid p_l = min(q, pmax_l), q = 1, 2, 4, ... (pmax_l: the largest power
- * of two with p_l^2 | n_l), on scratch buffers it allocates for the duration (2 N elements), and keeps
- * the fastest; the choice is remembered per (shape, dtype, direction, schedule, GPU) in the process's
- * wisdom table (fftu_wisdom_*).  If the scratch cannot be allocated, the default grid is used. */
+ * planner measures, on scratch buffers it allocates for the duration (2 N elements), one coordinate at
+ * a time: every candidate grid p_l = min(q, pmax_l), q = 1, 2, 4, ... (pmax_l: the largest power of two
+ * with p_l^2 | n_l); then, for the fastest grid, the schedules (AUTO, GENERIC_A, GENERIC) unless
+ * opts->schedule fixes one; then the strided passes' tile target (2048, 4096, 8192 for complex64;
+ * 1024, 2048, 4096 for complex128) and radix (8, 16) when the schedule has strided passes.  The choice
+ * is remembered per (shape, dtype, direction, requested schedule, GPU) in the process's wisdom table
+ * (fftu_wisdom_*).  If the scratch cannot be allocated, the defaults are used. */
 fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,
                          const fftu_options *opts, fftu_handle *out);
 
@@ -258,8 +267,9 @@ fftu_status fftu_batch_exec(fftu_batch batch, const void *const *ins, void *cons
 fftu_status fftu_batch_check_status(fftu_batch batch);
 fftu_status fftu_batch_destroy(fftu_batch batch);
 
-/* Wisdom: the tuned grids as text lines "fftu-wisdom-v1 <key> <p_1,...,p_d>".  Export writes the
- * process's table, import merges a file into it, forget clears it. */
+/* Wisdom: the tuned choices as text lines "fftu-wisdom-v2 <key> <p_1,...,p_d> <schedule> <tile> <radix>"
+ * (lines "fftu-wisdom-v1 <key> <p_1,...,p_d>" are read as grids with the other choices left to the
+ * defaults).  Export writes the process's table, import merges a file into it, forget clears it. */
 fftu_status fftu_wisdom_export(const char *path);
 fftu_status fftu_wisdom_import(const char *path);
 fftu_status fftu_wisdom_forget(void);

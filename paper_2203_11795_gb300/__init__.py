@@ -50,7 +50,8 @@ class FFTUError(RuntimeError):
 
 class fftu_options(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int), ("tune", ctypes.c_int), ("precision", ctypes.c_int),
-                ("layout", ctypes.c_int), ("workspace_mode", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("layout", ctypes.c_int), ("workspace_mode", ctypes.c_int), ("tile", ctypes.c_int),
+                ("radix", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class fftu_info(ctypes.Structure):
@@ -59,7 +60,8 @@ class fftu_info(ctypes.Structure):
                 ("launches_phase_a", ctypes.c_int), ("launches_phase_b", ctypes.c_int),
                 ("N", ctypes.c_int64), ("alg_bytes", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("tuned", ctypes.c_int), ("precision", ctypes.c_int),
-                ("workspace_need", ctypes.c_int64), ("layout", ctypes.c_int), ("workspace_mode", ctypes.c_int)]
+                ("workspace_need", ctypes.c_int64), ("layout", ctypes.c_int), ("workspace_mode", ctypes.c_int),
+                ("tile", ctypes.c_int), ("radix", ctypes.c_int)]
 
 
 class fftu_server_config(ctypes.Structure):
@@ -169,10 +171,10 @@ def fftu_plan(d: int, n, p, dtype: int, direction: int) -> int:
 
 def fftu_plan_ex(d: int, n, p, dtype: int, direction: int, schedule: int = FFTU_SCHED_AUTO,
                  tune: bool = False, precision: int = FFTU_PREC_NATIVE, layout: int = FFTU_LAYOUT_NATURAL,
-                 workspace_mode: int = FFTU_WORKSPACE_PLAN) -> int:
+                 workspace_mode: int = FFTU_WORKSPACE_PLAN, tile: int = 0, radix: int = 0) -> int:
     h = ctypes.c_void_p()
     opts = fftu_options(schedule=int(schedule), tune=int(bool(tune)), precision=int(precision), layout=int(layout),
-                        workspace_mode=int(workspace_mode))
+                        workspace_mode=int(workspace_mode), tile=int(tile), radix=int(radix))
     _check(_lib.fftu_plan_ex(int(d), _i64(n), _i64(p), int(dtype), int(direction), ctypes.byref(opts),
                              ctypes.byref(h)), "fftu_plan_ex")
     return h.value
@@ -205,7 +207,7 @@ def fftu_plan_info(plan: int) -> dict:
             "launches_phase_b": info.launches_phase_b, "N": info.N, "alg_bytes": info.alg_bytes,
             "table_bytes": info.table_bytes, "workspace_bytes": info.workspace_bytes, "tuned": info.tuned,
             "precision": info.precision, "workspace_need": info.workspace_need, "layout": info.layout,
-            "workspace_mode": info.workspace_mode}
+            "workspace_mode": info.workspace_mode, "tile": info.tile, "radix": info.radix}
 
 
 def fftu_check_device_status(plan: int) -> None:
@@ -331,7 +333,7 @@ class Plan:
 
     def __init__(self, n, p=None, dtype=None, inverse: bool = False, schedule: int = FFTU_SCHED_AUTO,
                  tune: bool = False, precision: int = FFTU_PREC_NATIVE, layout: int = FFTU_LAYOUT_NATURAL,
-                 workspace_mode: int = FFTU_WORKSPACE_PLAN):
+                 workspace_mode: int = FFTU_WORKSPACE_PLAN, tile: int = 0, radix: int = 0):
         import torch
         self.n = tuple(int(v) for v in n)
         self.dtype = dtype if dtype is not None else torch.complex64
@@ -339,7 +341,7 @@ class Plan:
         self.inverse = bool(inverse)
         self.handle = fftu_plan_ex(len(self.n), self.n, None if p is None else list(p), code,
                                    FFTU_INVERSE if inverse else FFTU_FORWARD, schedule, tune, precision, layout,
-                                   workspace_mode)
+                                   workspace_mode, tile, radix)
         self.p = tuple(self.info["p"])
 
     def _validate(self, t, name):

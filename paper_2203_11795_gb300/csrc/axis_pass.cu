@@ -59,14 +59,14 @@ __global__ void pointwise_kernel(C *out, const C *mul, int64_t n) {
         out[i] = cmul(out[i], mul[i]);
 }
 
-template <int DIR, int TCK>
+template <typename C, int DIR, int TCK>
 void launch_axis_tc(const AxisPass &a, unsigned grid, size_t smem, cudaStream_t st) {
     const int last = a.nstages > 0 ? a.radix[a.nstages - 1] : 1;
     switch (last) {
-        case 2: axis_pass_kernel<float2, DIR, 2, TCK><<<grid, a.threads, smem, st>>>(a); break;
-        case 4: axis_pass_kernel<float2, DIR, 4, TCK><<<grid, a.threads, smem, st>>>(a); break;
-        case 8: axis_pass_kernel<float2, DIR, 8, TCK><<<grid, a.threads, smem, st>>>(a); break;
-        default: axis_pass_kernel<float2, DIR, 1, TCK><<<grid, a.threads, smem, st>>>(a); break;
+        case 2: axis_pass_kernel<C, DIR, 2, TCK><<<grid, a.threads, smem, st>>>(a); break;
+        case 4: axis_pass_kernel<C, DIR, 4, TCK><<<grid, a.threads, smem, st>>>(a); break;
+        case 8: axis_pass_kernel<C, DIR, 8, TCK><<<grid, a.threads, smem, st>>>(a); break;
+        default: axis_pass_kernel<C, DIR, 1, TCK><<<grid, a.threads, smem, st>>>(a); break;
     }
 }
 
@@ -74,13 +74,17 @@ template <typename C, int DIR>
 cudaError_t launch_axis_t(const AxisPass &a, cudaStream_t st) {
     size_t smem = (size_t)a.tile * sizeof(C);
     int64_t grid = a.tiles < (int64_t)1 << 30 ? a.tiles : (int64_t)1 << 30;
+    if (a.tc == 3) {
+        launch_axis_tc<C, DIR, 3>(a, (unsigned)grid, smem, st);
+        return cudaGetLastError();
+    }
     if constexpr (sizeof(C) == 8) {
         if (a.tc == 1) {
-            launch_axis_tc<DIR, 1>(a, (unsigned)grid, smem, st);
+            launch_axis_tc<C, DIR, 1>(a, (unsigned)grid, smem, st);
             return cudaGetLastError();
         }
         if (a.tc == 2) {
-            launch_axis_tc<DIR, 2>(a, (unsigned)grid, smem, st);
+            launch_axis_tc<C, DIR, 2>(a, (unsigned)grid, smem, st);
             return cudaGetLastError();
         }
     }
@@ -106,6 +110,10 @@ cudaError_t prepare_axis_t() {
     if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 2>();
     if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 4>();
     if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 16>();
+    if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 1, 3>();
+    if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 2, 3>();
+    if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 4, 3>();
+    if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 8, 3>();
     if constexpr (sizeof(C) == 8) {
         if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 1, 1>();
         if (e == cudaSuccess) e = prepare_axis_r<C, DIR, 2, 1>();

@@ -202,8 +202,8 @@ fftu_status batch_create(int count, const fftu_handle *plans, Batch **out_batch)
             record_error("batch: CYCLIC-layout plans are not batched");
             return FFTU_ERR_UNSUPPORTED;
         }
-        if (views[i].precision != 0) {
-            record_error("batch: split-precision plans are not batched");
+        if (views[i].precision != 0 || views[i].radix != 8) {
+            record_error("batch: split-precision and radix-16 plans are not batched");
             return FFTU_ERR_UNSUPPORTED;
         }
         if (views[i].pingpong) {

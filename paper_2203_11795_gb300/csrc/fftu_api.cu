@@ -116,6 +116,8 @@ struct Plan {
     size_t ring_counter_off = 0; // ring schedule: offset of its counters in the workspace
     int layout = 0;              // fftu_layout
     int workspace_mode = 0;      // fftu_workspace_mode
+    int tile = 0;                // whole-line tile target of the strided passes (0 = default)
+    int radix = 8;               // 8 or 16: stage radix of the strided passes
     int *dstatus = nullptr;
     int tuned = 0;
     std::vector<Step> phase_a, phase_b;
@@ -139,7 +141,7 @@ fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPa
     for (int k = 0; k < l; ++k) outer *= pl.n[k];
     for (int k = l + 1; k < pl.d; ++k) inner *= pl.n[k];
     const int64_t nl = pl.n[l], Ll = pl.n[l] / pl.p[l];
-    const int64_t target = is_double ? kTileTargetC128 : kTileTargetC64;
+    const int64_t target = pl.tile > 0 ? pl.tile : (is_double ? kTileTargetC128 : kTileTargetC64);
     const int64_t maxtile = is_double ? kMaxGenericTile / 4 : kMaxGenericTile / 2;
     a.outer = outer;
     a.inner = inner;
@@ -196,7 +198,8 @@ fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPa
     a.threads = th;
     a.tw = pl.table(l);
     a.scale = scale;
-    a.tc = pl.precision;
+    // tc: 1 / 2 split-precision tensor-core radix-16 stages, 3 CUDA-core radix-16 stages, 0 radix 8
+    a.tc = pl.precision ? pl.precision : (pl.radix == 16 ? 3 : 0);
     a.nstages = a.tc ? radix_plan_tc(a.len, a.radix) : radix_plan(a.len, a.radix);
     return FFTU_OK;
 }
@@ -445,6 +448,7 @@ fftu_status plan_view(fftu_handle h, PlanView *v) {
     v->pingpong = pl.generic_pingpong;
     v->precision = pl.precision;
     v->layout = pl.layout;
+    v->radix = pl.radix;
     v->a_passes.clear();
     v->b_steps.clear();
     const bool fused_a = !pl.phase_a.empty() && pl.phase_a[0].kind == STEP_PHASE_A3;
@@ -519,6 +523,16 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
         set_err("unknown workspace mode %d", ws_mode);
         return FFTU_ERR_ARG;
     }
+    int tile = opts ? opts->tile : 0;
+    int radix = opts && opts->radix ? opts->radix : 8;
+    if (tile != 0 && (tile < 1024 || tile > (dtype == FFTU_C128 ? 4096 : 8192) || (tile & (tile - 1)))) {
+        set_err("tile must be 0 or a power of two in [1024, %d]", dtype == FFTU_C128 ? 4096 : 8192);
+        return FFTU_ERR_ARG;
+    }
+    if (radix != 8 && radix != 16) {
+        set_err("radix must be 0, 8 or 16");
+        return FFTU_ERR_ARG;
+    }
     if (precision != FFTU_PREC_NATIVE) {
         if (dtype != FFTU_C64) {
             set_err("split-precision tensor-core stages are for complex64 plans");
@@ -573,9 +587,14 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
         }
     int tuned = 0;
     if (!p && opts && opts->tune) {
-        int64_t tp[FFTU_MAX_DIMS];
-        if (autotune_grid(d, n, dtype, dir, sched, tp)) {
-            for (int l = 0; l < d; ++l) pp[l] = tp[l];
+        fftu_options base = *opts;
+        base.schedule = sched;
+        TuneChoice tc;
+        if (autotune(d, n, dtype, dir, base, &tc)) {
+            for (int l = 0; l < d; ++l) pp[l] = tc.p[l];
+            sched = tc.schedule;
+            if (tc.tile) tile = tc.tile;
+            if (tc.radix) radix = tc.radix;
             tuned = 1;
         }
         g_err[0] = '\0';
@@ -597,6 +616,8 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
     pl->precision = precision;
     pl->layout = layout;
     pl->workspace_mode = ws_mode;
+    pl->tile = tile;
+    pl->radix = radix;
     pl->N = N;
     pl->esize = dtype == FFTU_C128 ? 16 : 8;
     cudaError_t e = cudaGetDevice(&pl->device);
@@ -913,6 +934,8 @@ fftu_status fftu_plan_info(fftu_handle h, fftu_info *info) {
     info->workspace_need = (int64_t)pl->ws_need;
     info->layout = pl->layout;
     info->workspace_mode = pl->workspace_mode;
+    info->tile = pl->tile > 0 ? pl->tile : (pl->dtype == FFTU_C128 ? (int)kTileTargetC128 : (int)kTileTargetC64);
+    info->radix = pl->radix;
     return FFTU_OK;
 }
 

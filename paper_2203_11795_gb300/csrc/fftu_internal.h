@@ -44,7 +44,8 @@ struct AxisPass {
     int nstages;
     int radix[kMaxStages];
     int64_t tiles;
-    int tc;           // 0: CUDA-core stages; 1 / 2: radix-16 stages as split bfloat16 / float16 MMAs
+    int tc;           // 0: radix 8 after a smaller first stage; 1 / 2: radix-16 stages as split bfloat16 /
+                      // float16 MMAs; 3: radix-16 CUDA-core stages; (1-3: the remaining factor last)
 };
 
 // Phase B on the d-dim groups {m + s' (n/p)} with every p_l <= 16, in one pass.
@@ -101,6 +102,7 @@ struct PlanView {
     bool pingpong;                  // phase A alternates with a workspace (long lines)
     int precision;                  // fftu_precision of the plan's radix-16 stages
     int layout;                     // fftu_layout
+    int radix;                      // stage radix of the strided passes (8 or 16)
     std::vector<StepView> a_passes;  // phase A, generic passes (first reads in, then in place on out)
     std::vector<StepView> b_steps;   // phase B, in place on out
 };
@@ -111,8 +113,13 @@ fftu_status plan_view(fftu_handle h, PlanView *v);
 cudaError_t launch_cyclic_permute(const void *src, void *dst, int d, const int64_t *n, const int64_t *p,
                                   int is_double, int to_cyclic, cudaStream_t st);
 
-// Plan-time tuning of p (tuner.cu); false: use the default grid.
-bool autotune_grid(int d, const int64_t *n, fftu_dtype dtype, fftu_dir dir, int sched, int64_t *p_out);
+// Plan-time tuning (tuner.cu): fills the grid and the choices `base` leaves open (schedule AUTO,
+// tile 0, radix 0); false: use the defaults.
+struct TuneChoice {
+    int64_t p[FFTU_MAX_DIMS];
+    int schedule, tile, radix;
+};
+bool autotune(int d, const int64_t *n, fftu_dtype dtype, fftu_dir dir, const fftu_options &base, TuneChoice *t);
 
 // Set the calling thread's detail string returned by fftu_last_error().
 void record_error(const char *msg);

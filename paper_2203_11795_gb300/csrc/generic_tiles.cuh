@@ -291,6 +291,7 @@ __device__ __forceinline__ void stockham_stage_tc16(float2 *sm, const float2 *__
 // One tile of a generic strided pass (see AxisPass): load, Stockham stages, permuted store.
 // TCK = 0: radix R0 first, then radix 8 (CUDA cores).  TCK = 1 / 2: radix-16 stages as split
 // bfloat16 / float16 tensor-core contractions, then one CUDA-core stage of radix R0 (the rest of len).
+// TCK = 3: radix-16 CUDA-core stages, then one stage of radix R0.
 template <typename C, int DIR, int R0, int TCK = 0>
 __device__ __forceinline__ void axis_tile(const AxisPass &a, int64_t t, C *sm, const C *__restrict__ src,
                                           C *__restrict__ dst, const C *__restrict__ tw) {
@@ -332,6 +333,11 @@ __device__ __forceinline__ void axis_tile(const AxisPass &a, int64_t t, C *sm, c
             Ns = R0;
         }
         for (; Ns < a.len; Ns *= 8) stockham_stage<C, DIR, 8>(sm, tw, a, Ns, tid, nt);
+    } else if constexpr (TCK == 3) {
+        for (; Ns * 16 <= a.len; Ns *= 16) stockham_stage<C, DIR, 16>(sm, tw, a, Ns, tid, nt);
+        if constexpr (R0 > 1) {
+            if (Ns < a.len) stockham_stage<C, DIR, R0>(sm, tw, a, Ns, tid, nt);
+        }
     } else {
         static_assert(sizeof(C) == 8, "split-precision stages are for complex64");
         Dft16Frags<DIR, TCK> F;

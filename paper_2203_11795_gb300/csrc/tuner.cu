@@ -1,16 +1,20 @@
-// Plan-time tuning of the cyclic grid p (the analogue of FFTW's measured planning,
-// which the paper's FFTU relies on for its local FFTs, Sec. 4.1).
+// Plan-time tuning (the analogue of FFTW's measured planning, which the paper's FFTU relies on
+// for its local FFTs, Sec. 4.1), over the choices this library adds: the cyclic grid p, the
+// kernel schedule, and the strided passes' tile size and stage radix.
 //
-// For a problem with p left to the library, every candidate grid is planned, run on
-// scratch buffers and timed with CUDA events in the plan's own direction; the fastest wins.
-// Candidates: p_l = min(q, pmax_l) for q = 1, 2, 4, ..., where pmax_l is the largest
-// power of two with p_l^2 | n_l (Algorithm 2.3's condition); the untuned default grid
-// (q = 8) is one of them.
-// Results are kept per (shape, dtype, direction, schedule, GPU name) in an in-process
-// table that can be written to and read from a text file ("wisdom").
+// Every candidate is planned, run once on scratch buffers, then timed with CUDA events (best of
+// three executions, the plan's own direction).  The search takes one coordinate at a time:
+//   1. p: p_l = min(q, pmax_l) for q = 1, 2, 4, ..., where pmax_l is the largest power of two with
+//      p_l^2 | n_l (Algorithm 2.3's condition); the untuned default (q = 8) is one of them;
+//   2. for that p, the schedule (AUTO, GENERIC_A, GENERIC), unless the caller fixed one;
+//   3. the whole-line tile target of the strided passes, unless fixed;
+//   4. their stage radix (8 or 16), unless fixed.
+// Results are kept per (shape, dtype, direction, requested schedule, precision, GPU name) in an
+// in-process table that can be written to and read from a text file ("wisdom").
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -23,29 +27,37 @@ namespace fftu {
 
 namespace {
 
-std::mutex g_wisdom_mutex;
-std::map<std::string, std::vector<int64_t>> g_wisdom;
+struct Wise {
+    std::vector<int64_t> p;
+    int schedule = 0, tile = 0, radix = 0;  // 0: not chosen (the plan's default)
+};
 
-std::string wisdom_key(int d, const int64_t *n, int dtype, int dir, int sched) {
+std::mutex g_wisdom_mutex;
+std::map<std::string, Wise> g_wisdom;
+
+std::string gpu_name() {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceProp prop;
     std::string name = "unknown";
     if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    else cudaGetLastError();
     for (char &c : name)
         if (c == ' ') c = '_';
+    return name;
+}
+
+std::string wisdom_key(int d, const int64_t *n, int dtype, int dir, int sched, int precision) {
     std::string k = std::to_string(d) + ":";
     for (int l = 0; l < d; ++l) k += (l ? "," : "") + std::to_string(n[l]);
-    k += ":" + std::to_string(dtype) + ":" + std::to_string(dir) + ":" + std::to_string(sched) + ":" + name;
+    k += ":" + std::to_string(dtype) + ":" + std::to_string(dir) + ":" + std::to_string(sched) + ":" +
+         std::to_string(precision) + ":" + gpu_name();
     return k;
 }
 
 // Time one candidate: best of three executions after one warm-up; < 0 on failure.
-float time_candidate(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir, int sched,
-                     void *in, void *out) {
-    fftu_options o;
-    std::memset(&o, 0, sizeof(o));
-    o.schedule = sched;
+float time_candidate(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,
+                     const fftu_options &o, void *in, void *out) {
     fftu_handle h = nullptr;
     if (fftu_plan_ex(d, n, p, dtype, dir, &o, &h) != FFTU_OK) return -1.f;
     cudaEvent_t e0, e1;
@@ -72,15 +84,18 @@ float time_candidate(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype
 
 }  // namespace
 
-// p_out receives the chosen grid; returns true when tuning ran (or wisdom answered),
-// false when the caller should fall back to the default grid (no memory, no candidates).
-bool autotune_grid(int d, const int64_t *n, fftu_dtype dtype, fftu_dir dir, int sched, int64_t *p_out) {
-    const std::string key = wisdom_key(d, n, dtype, dir, sched);
+// Fills `t` (p, and schedule / tile / radix where the caller left them open); returns true when
+// tuning ran or wisdom answered, false when the caller should use the defaults.
+bool autotune(int d, const int64_t *n, fftu_dtype dtype, fftu_dir dir, const fftu_options &base, TuneChoice *t) {
+    const std::string key = wisdom_key(d, n, dtype, dir, base.schedule, base.precision);
     {
         std::lock_guard<std::mutex> lock(g_wisdom_mutex);
         auto it = g_wisdom.find(key);
-        if (it != g_wisdom.end() && (int)it->second.size() == d) {
-            for (int l = 0; l < d; ++l) p_out[l] = it->second[l];
+        if (it != g_wisdom.end() && (int)it->second.p.size() == d) {
+            for (int l = 0; l < d; ++l) t->p[l] = it->second.p[l];
+            t->schedule = it->second.schedule ? it->second.schedule : base.schedule;
+            t->tile = it->second.tile ? it->second.tile : base.tile;
+            t->radix = it->second.radix ? it->second.radix : base.radix;
             return true;
         }
     }
@@ -91,17 +106,6 @@ bool autotune_grid(int d, const int64_t *n, fftu_dtype dtype, fftu_dir dir, int 
         while (n[l] % ((2 * q) * (2 * q)) == 0) q *= 2;
         pmax[l] = q;
     }
-    std::vector<std::vector<int64_t>> cands;
-    for (int64_t q = 1;; q *= 2) {
-        std::vector<int64_t> c(d);
-        bool grew = false;
-        for (int l = 0; l < d; ++l) {
-            c[l] = q < pmax[l] ? q : pmax[l];
-            if (q <= pmax[l]) grew = true;
-        }
-        cands.push_back(c);
-        if (!grew) break;
-    }
     const size_t bytes = (size_t)N * (dtype == FFTU_C128 ? 16 : 8);
     void *in = nullptr, *out = nullptr;
     if (cudaMalloc(&in, bytes) != cudaSuccess || cudaMalloc(&out, bytes) != cudaSuccess) {
@@ -110,21 +114,66 @@ bool autotune_grid(int d, const int64_t *n, fftu_dtype dtype, fftu_dir dir, int 
         return false;
     }
     cudaMemset(in, 0, bytes);
-    float best = -1.f;
+
+    fftu_options cur = base;
+    cur.tune = 0;
     std::vector<int64_t> best_p;
-    for (const auto &c : cands) {
-        const float ms = time_candidate(d, n, c.data(), dtype, dir, sched, in, out);
+    float best = -1.f;
+    // 1. the grid
+    for (int64_t q = 1;; q *= 2) {
+        std::vector<int64_t> c(d);
+        bool grew = false;
+        for (int l = 0; l < d; ++l) {
+            c[l] = q < pmax[l] ? q : pmax[l];
+            if (q <= pmax[l]) grew = true;
+        }
+        const float ms = time_candidate(d, n, c.data(), dtype, dir, cur, in, out);
         if (ms >= 0.f && (best < 0.f || ms < best)) {
             best = ms;
             best_p = c;
         }
+        if (!grew) break;
     }
+    if (best_p.empty()) {
+        cudaFree(in);
+        cudaFree(out);
+        return false;
+    }
+    // 2-4. schedule, tile, radix, each with the others at their best so far
+    auto try_field = [&](int *field, std::initializer_list<int> values) {
+        const int keep = *field;
+        int best_v = keep;
+        for (int v : values) {
+            if (v == keep) continue;
+            *field = v;
+            const float ms = time_candidate(d, n, best_p.data(), dtype, dir, cur, in, out);
+            if (ms >= 0.f && ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        *field = best_v;
+    };
+    if (base.schedule == FFTU_SCHED_AUTO && base.precision == FFTU_PREC_NATIVE)
+        try_field(&cur.schedule, {FFTU_SCHED_GENERIC_A, FFTU_SCHED_GENERIC});
+    if (base.tile == 0) {
+        if (dtype == FFTU_C128) try_field(&cur.tile, {1024, 4096});
+        else try_field(&cur.tile, {2048, 8192});
+    }
+    if (base.radix == 0 && base.precision == FFTU_PREC_NATIVE) try_field(&cur.radix, {16});
     cudaFree(in);
     cudaFree(out);
-    if (best_p.empty()) return false;
-    for (int l = 0; l < d; ++l) p_out[l] = best_p[l];
+    for (int l = 0; l < d; ++l) t->p[l] = best_p[l];
+    t->schedule = cur.schedule;
+    t->tile = cur.tile;
+    t->radix = cur.radix;
+    Wise w;
+    w.p = best_p;
+    w.schedule = cur.schedule;
+    w.tile = cur.tile;
+    w.radix = cur.radix;
     std::lock_guard<std::mutex> lock(g_wisdom_mutex);
-    g_wisdom[key] = best_p;
+    g_wisdom[key] = w;
     return true;
 }
 
@@ -141,9 +190,10 @@ fftu_status fftu_wisdom_export(const char *path) {
     }
     std::lock_guard<std::mutex> lock(fftu::g_wisdom_mutex);
     for (const auto &kv : fftu::g_wisdom) {
-        std::fprintf(f, "fftu-wisdom-v1 %s", kv.first.c_str());
-        for (size_t l = 0; l < kv.second.size(); ++l) std::fprintf(f, "%s%lld", l ? "," : " ", (long long)kv.second[l]);
-        std::fprintf(f, "\n");
+        std::fprintf(f, "fftu-wisdom-v2 %s", kv.first.c_str());
+        for (size_t l = 0; l < kv.second.p.size(); ++l)
+            std::fprintf(f, "%s%lld", l ? "," : " ", (long long)kv.second.p[l]);
+        std::fprintf(f, " %d %d %d\n", kv.second.schedule, kv.second.tile, kv.second.radix);
     }
     std::fclose(f);
     return FFTU_OK;
@@ -156,13 +206,29 @@ fftu_status fftu_wisdom_import(const char *path) {
         fftu::record_error("wisdom: cannot open the file for reading");
         return FFTU_ERR_ARG;
     }
-    char tag[32], key[512], vals[256];
     std::lock_guard<std::mutex> lock(fftu::g_wisdom_mutex);
-    while (std::fscanf(f, "%31s %511s %255s", tag, key, vals) == 3) {
-        if (std::strcmp(tag, "fftu-wisdom-v1") != 0) continue;
-        std::vector<int64_t> p;
-        for (char *tok = std::strtok(vals, ","); tok; tok = std::strtok(nullptr, ",")) p.push_back(std::atoll(tok));
-        fftu::g_wisdom[key] = p;
+    char line[1024];
+    while (std::fgets(line, sizeof(line), f)) {
+        char tag[32], key[512], vals[256];
+        int sched = 0, tile = 0, radix = 0;
+        const int got = std::sscanf(line, "%31s %511s %255s %d %d %d", tag, key, vals, &sched, &tile, &radix);
+        if (got < 3) continue;
+        std::string k = key;
+        if (std::strcmp(tag, "fftu-wisdom-v1") == 0) {
+            // v1 keys carry no precision field: d:n:dtype:dir:sched:gpu -> d:n:dtype:dir:sched:0:gpu
+            const size_t pos = k.rfind(':');
+            if (pos == std::string::npos) continue;
+            k.insert(pos, ":0");
+            sched = tile = radix = 0;
+        } else if (!(got == 6 && std::strcmp(tag, "fftu-wisdom-v2") == 0)) {
+            continue;
+        }
+        fftu::Wise w;
+        for (char *tok = std::strtok(vals, ","); tok; tok = std::strtok(nullptr, ",")) w.p.push_back(std::atoll(tok));
+        w.schedule = sched;
+        w.tile = tile;
+        w.radix = radix;
+        fftu::g_wisdom[k] = w;
     }
     std::fclose(f);
     return FFTU_OK;

@@ -277,3 +277,29 @@ def test_pointwise_rejects_mismatched_plans(fftu):
                 fftu.fftu_exec_pointwise(a.handle, b.handle, x.data_ptr(), x.data_ptr(), x.data_ptr() + 0,
                                          x.data_ptr(), 0)
             assert ei.value.status == 1
+
+
+# ---- strided-pass tile target and radix (the tuner's other coordinates) -----------------------
+
+@pytest.mark.parametrize("case", [((64, 64, 64), (4, 4, 4), np.complex64),
+                                  ((256, 64), (4, 2), np.complex64),
+                                  ((32, 32, 32, 32), (2, 2, 2, 2), np.complex128),
+                                  ((8192,), (4,), np.complex64),
+                                  ((32768,), (128,), np.complex64)], ids=_id)
+@pytest.mark.parametrize("tile,radix", [(0, 16), (2048, 8), (8192, 16), (1024, 16)])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_tile_and_radix_options(fftu, case, tile, radix, inverse):
+    import torch
+    shape, p, dt = case
+    if dt == np.complex128 and tile == 8192:
+        pytest.skip("complex128 tiles stop at 4096")
+    x = complex_uniform(616, shape, dtype=dt)
+    t = torch.from_numpy(x).cuda()
+    with fftu.Plan(shape, p, dtype=t.dtype, inverse=inverse, schedule=fftu.FFTU_SCHED_GENERIC, tile=tile,
+                   radix=radix) as plan:
+        assert plan.info["radix"] == radix and (tile == 0 or plan.info["tile"] == tile)
+        y = plan.exec(t)
+        torch.cuda.synchronize()
+        plan.check_device_status()
+    ref = oracle.fftn(x.astype(np.complex128), inverse=inverse)
+    assert oracle.rel_l2(y.cpu().numpy(), ref) <= tolerance(dt, x.size)

@@ -25,7 +25,7 @@ def fftu():
 def _key(shape, dtype_code, direction):
     import torch
     name = torch.cuda.get_device_name(0).replace(" ", "_")
-    return f"{len(shape)}:{','.join(str(v) for v in shape)}:{dtype_code}:{direction}:0:{name}"
+    return f"{len(shape)}:{','.join(str(v) for v in shape)}:{dtype_code}:{direction}:0:0:{name}"
 
 
 @pytest.mark.parametrize("shape,inverse", [((64, 64, 64), False), ((128, 32), True), ((16, 16, 16, 16), False)])
@@ -48,21 +48,27 @@ def test_tuned_plan_is_valid_and_correct(fftu, tmp_path, shape, inverse):
     fftu.fftu_wisdom_export(str(path))
     code = fftu.FFTU_C64
     direction = fftu.FFTU_INVERSE if inverse else fftu.FFTU_FORWARD
-    line = f"fftu-wisdom-v1 {_key(shape, code, direction)} {','.join(str(v) for v in info['p'])}"
-    assert line in path.read_text().splitlines()
+    lines = [ln for ln in path.read_text().splitlines() if ln.split()[1] == _key(shape, code, direction)]
+    assert len(lines) == 1
+    tag, _, grid, sched, tile, radix = lines[0].split()
+    assert tag == "fftu-wisdom-v2" and grid == ",".join(str(v) for v in info["p"])
+    assert int(sched) == info["schedule"] or (int(sched) == 0 and info["schedule"] == fftu.FFTU_SCHED_FUSED)
+    assert int(tile) in (0, info["tile"]) and int(radix) in (0, info["radix"])
 
 
 def test_imported_wisdom_is_obeyed(fftu, tmp_path):
     import torch
     shape = (32, 32, 32)
     path = tmp_path / "w.txt"
-    path.write_text(f"fftu-wisdom-v1 {_key(shape, fftu.FFTU_C64, fftu.FFTU_FORWARD)} 2,1,4\n")
+    path.write_text(f"fftu-wisdom-v2 {_key(shape, fftu.FFTU_C64, fftu.FFTU_FORWARD)} 2,1,4 3 2048 16\n")
     fftu.fftu_wisdom_forget()
     fftu.fftu_wisdom_import(str(path))
     x = complex_uniform(8, shape, dtype=np.complex64)
     t = torch.from_numpy(x).cuda()
     with fftu.Plan(shape, None, dtype=t.dtype, tune=True) as plan:
-        assert plan.info["p"] == [2, 1, 4] and plan.info["tuned"] == 1
+        info = plan.info
+        assert info["p"] == [2, 1, 4] and info["tuned"] == 1
+        assert info["schedule"] == fftu.FFTU_SCHED_GENERIC_A and info["tile"] == 2048 and info["radix"] == 16
         out = plan.exec(t)
         torch.cuda.synchronize()
     assert oracle.rel_l2(out.cpu().numpy(), oracle.fftn(x.astype(np.complex128))) < 1e-4
