@@ -285,6 +285,14 @@ fftu_status fftu_workspace_size(fftu_handle plan, size_t *bytes);
  * set a stream's workspace before its exec and order them. */
 fftu_status fftu_set_workspace(fftu_handle plan, void *workspace, size_t bytes);
 
+/* Failure-detection self-test (no counterpart in the paper): runs the bounded device wait the batch
+ * kernel uses on a device word that nothing ever advances, with a budget of limit_s seconds
+ * (0.001..2).  The wait must give up and report FFTU_ERR_TIMEOUT through its status word, as any
+ * expired wait in this library does instead of trapping; *waited_s (may be NULL) receives the time
+ * it waited.  Returns FFTU_OK when that happened, FFTU_ERR_INTERNAL if the status was not set.
+ * Synchronises its own stream; the context stays usable. */
+fftu_status fftu_selftest_bounded_wait(double limit_s, double *waited_s);
+
 /* Static string for a status code. */
 const char *fftu_status_string(fftu_status s);
 

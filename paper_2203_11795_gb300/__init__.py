@@ -34,7 +34,8 @@ EXPORTS = ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_ex
            "fftu_plan_info",
            "fftu_check_device_status", "fftu_exec_noalloc", "fftu_batch_create", "fftu_batch_exec",
            "fftu_batch_check_status", "fftu_batch_destroy", "fftu_wisdom_export", "fftu_wisdom_import",
-           "fftu_wisdom_forget", "fftu_workspace_size", "fftu_set_workspace", "fftu_status_string",
+           "fftu_wisdom_forget", "fftu_workspace_size", "fftu_set_workspace", "fftu_selftest_bounded_wait",
+           "fftu_status_string",
            "fftu_last_error", "fftu_version",
            # include/fftu_serve.h
            "fftu_server_create", "fftu_server_submit", "fftu_server_poll", "fftu_server_drain",
@@ -114,6 +115,7 @@ def _load_library() -> ctypes.CDLL:
     lib.fftu_wisdom_forget.argtypes = []
     lib.fftu_workspace_size.argtypes = [h, ctypes.POINTER(ctypes.c_size_t)]
     lib.fftu_set_workspace.argtypes = [h, vp, ctypes.c_size_t]
+    lib.fftu_selftest_bounded_wait.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     lib.fftu_server_create.argtypes = [ctypes.POINTER(fftu_server_config), ctypes.POINTER(h)]
     lib.fftu_server_submit.argtypes = [h, ctypes.POINTER(fftu_request)]
     lib.fftu_server_poll.argtypes = [h, ctypes.POINTER(fftu_completion), ctypes.c_int]
@@ -128,6 +130,7 @@ def _load_library() -> ctypes.CDLL:
                  "fftu_plan_info", "fftu_check_device_status", "fftu_exec_noalloc", "fftu_batch_create",
                  "fftu_batch_exec", "fftu_batch_check_status", "fftu_batch_destroy", "fftu_wisdom_export",
                  "fftu_wisdom_import", "fftu_wisdom_forget", "fftu_workspace_size", "fftu_set_workspace",
+                 "fftu_selftest_bounded_wait",
                  "fftu_server_create", "fftu_server_submit",
                  "fftu_server_poll", "fftu_server_drain", "fftu_server_stats_get", "fftu_server_destroy"):
         getattr(lib, name).restype = ctypes.c_int
@@ -303,6 +306,13 @@ def fftu_workspace_size(plan: int) -> int:
 
 def fftu_set_workspace(plan: int, ptr, nbytes: int) -> None:
     _check(_lib.fftu_set_workspace(plan, ptr, int(nbytes)), "fftu_set_workspace")
+
+
+def fftu_selftest_bounded_wait(limit_s: float) -> float:
+    """Seconds the device waited before its bounded wait gave up with FFTU_ERR_TIMEOUT."""
+    w = ctypes.c_double()
+    _check(_lib.fftu_selftest_bounded_wait(float(limit_s), ctypes.byref(w)), "fftu_selftest_bounded_wait")
+    return w.value
 
 
 def fftu_status_string(status: int) -> str:

@@ -18,6 +18,7 @@
 #include <new>
 #include <vector>
 
+#include "bounded_wait.cuh"
 #include "fft_device.cuh"
 #include "fftu_internal.h"
 #include "generic_tiles.cuh"
@@ -56,12 +57,6 @@ struct BatchParams {
     void *out[kMaxBatch];
 };
 
-__device__ __forceinline__ unsigned long long gtimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 // Each radix variant of the axis tile is its own function so that one kernel can hold
 // all of them without the register allocation of the largest applying to the rest.
 template <typename C, int DIR, int R0>
@@ -99,21 +94,9 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const __grid_const
                 s_jobi = lo;
                 int ok = 1;
                 const int dep = P.jobs[lo].dep;
-                if (dep >= 0) {
-                    const unsigned target = (unsigned)P.jobs[lo].dep_tiles;
-                    const unsigned long long t0 = gtimer_ns();
-                    for (;;) {
-                        unsigned v;
-                        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(P.done + dep) : "memory");
-                        if (v >= target) break;
-                        if ((long long)(gtimer_ns() - t0) > P.spin_limit_ns) {
-                            atomicCAS(P.status, 0, (int)FFTU_ERR_TIMEOUT);
-                            ok = 0;
-                            break;
-                        }
-                        __nanosleep(64);
-                    }
-                }
+                if (dep >= 0 &&
+                    !wait_counter_geq(P.done + dep, (unsigned)P.jobs[lo].dep_tiles, P.spin_limit_ns, P.status))
+                    ok = 0;
                 s_ok = ok;
             }
         }
@@ -151,6 +134,18 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const __grid_const
             atomicAdd(P.done + j, 1u);
         }
     }
+}
+
+// Diagnostic for fftu_selftest_bounded_wait: one thread waits, with the batch kernel's bounded
+// wait, on words[0], which nothing advances; the expired wait leaves FFTU_ERR_TIMEOUT in words[1]
+// and the time it waited in words[2..3].
+__global__ void wait_probe_kernel(unsigned *words, long long limit_ns) {
+    if (threadIdx.x != 0) return;
+    const unsigned long long t0 = globaltimer_ns();
+    wait_counter_geq(words, 1u, limit_ns, reinterpret_cast<int *>(words + 1));
+    const unsigned long long dt = globaltimer_ns() - t0;
+    words[2] = (unsigned)dt;
+    words[3] = (unsigned)(dt >> 32);
 }
 
 template <typename C, int DIR>
@@ -429,6 +424,44 @@ fftu_status fftu_batch_destroy(fftu_batch batch) {
     if (!batch) return FFTU_OK;
     fftu::batch_destroy(batch->impl);
     delete batch;
+    return FFTU_OK;
+}
+
+fftu_status fftu_selftest_bounded_wait(double limit_s, double *waited_s) {
+    using namespace fftu;
+    if (!(limit_s >= 1e-3 && limit_s <= 2.0)) {
+        record_error("selftest: limit_s must be in [0.001, 2]");
+        return FFTU_ERR_ARG;
+    }
+    // words: [0] the counter nothing advances, [1] status, [2..3] waited nanoseconds
+    unsigned *words = nullptr;
+    cudaError_t e = cudaMalloc(&words, 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return FFTU_ERR_NOMEM;
+    }
+    cudaStream_t ps = nullptr;
+    e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemsetAsync(words, 0, 16, ps);
+    if (e == cudaSuccess) {
+        wait_probe_kernel<<<1, 32, 0, ps>>>(words, (long long)(limit_s * 1e9));
+        e = cudaGetLastError();
+    }
+    unsigned host[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, words, 16, cudaMemcpyDeviceToHost, ps);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
+    if (ps) cudaStreamDestroy(ps);
+    cudaFree(words);
+    if (e != cudaSuccess) {
+        record_error("selftest: CUDA call failed");
+        return FFTU_ERR_CUDA;
+    }
+    unsigned long long ns = (unsigned long long)host[2] | ((unsigned long long)host[3] << 32);
+    if (waited_s) *waited_s = (double)ns * 1e-9;
+    if ((int)host[1] != (int)FFTU_ERR_TIMEOUT) {
+        record_error("selftest: the wait did not report FFTU_ERR_TIMEOUT");
+        return FFTU_ERR_INTERNAL;
+    }
     return FFTU_OK;
 }
 

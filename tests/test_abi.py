@@ -109,3 +109,11 @@ def test_layout_and_workspace_validation():
         f.fftu_workspace_size(None)
     with pytest.raises(f.FFTUError):
         f.fftu_set_workspace(None, None, 0)
+
+
+def test_selftest_limit_validation():
+    import paper_2203_11795_gb300 as f
+    for bad in (0.0, 5.0, float("nan")):
+        with pytest.raises(f.FFTUError) as ei:
+            f.fftu_selftest_bounded_wait(bad)
+        assert ei.value.status == 1
