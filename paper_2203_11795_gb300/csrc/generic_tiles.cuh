@@ -26,6 +26,12 @@ template <typename C> __device__ __forceinline__ void async_copy(C *dst_shared, 
 
 __device__ __forceinline__ void async_copy_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Two adjacent complex64 elements in one 16-byte copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void async_copy_pair(float2 *dst_shared, const float2 *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_shared);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 
 template <typename C, int DIR, int R>
 __device__ __forceinline__ void stockham_stage(C *sm, const C *__restrict__ tw, const AxisPass &a, int Ns,
@@ -308,8 +314,29 @@ __device__ __forceinline__ void axis_tile(const AxisPass &a, int64_t t, C *sm, c
         const int64_t tpo_mask = ((int64_t)1 << a.lg_tpo) - 1;
         gbase = (tt >> a.lg_tpo) * (int64_t)a.nl * a.inner + ((tt & tpo_mask) << a.lg_V);
     }
+    // complex64 tiles whose elements 2k and 2k + 1 are adjacent in global memory (runs of Gt >= 2
+    // classes along a line, or vectors of a strided axis): loads and stores go in 16-byte pairs with
+    // one index computation per pair.
+    const bool pairs = sizeof(C) == 8 && (a.contiguous ? a.Gt >= 2 && (a.mode == 1 || a.len >= 2) : a.V >= 2);
     // load: shared index e is the natural order of the tile (tile line position lp, vector v);
     // tile position lp = c_local + j Gt holds line position c0 + c_local + j G
+    if (pairs) {
+        const int half = a.tile >> 1;
+        for (int e2 = tid; e2 < half; e2 += nt) {
+            const int e = e2 << 1;
+            int lp, v;
+            if (a.contiguous) {
+                v = e >> a.lg_nlt;
+                lp = e & (a.nlt - 1);
+            } else {
+                lp = e >> a.lg_V;
+                v = e & (a.V - 1);
+            }
+            const int64_t gp = c0 + (lp & (a.Gt - 1)) + ((int64_t)(lp >> a.lg_Gt) << a.lg_G);
+            const int64_t g = a.contiguous ? gbase + (int64_t)v * a.nl + gp : gbase + gp * a.inner + v;
+            async_copy_pair(reinterpret_cast<float2 *>(sm + e), reinterpret_cast<const float2 *>(src + g));
+        }
+    } else
     for (int e = tid; e < a.tile; e += nt) {
         int lp, v;
         if (a.contiguous) {
@@ -350,6 +377,57 @@ __device__ __forceinline__ void axis_tile(const AxisPass &a, int64_t t, C *sm, c
 
     // store with the output permutation, twiddle and scale
     const Rl scale = (Rl)a.scale;
+    if (pairs) {
+        const int half = a.tile >> 1;
+        for (int e2 = tid; e2 < half; e2 += nt) {
+            const int e = e2 << 1;
+            int lpo, v;
+            if (a.contiguous) {
+                v = e >> a.lg_nlt;
+                lpo = e & (a.nlt - 1);
+            } else {
+                lpo = e >> a.lg_V;
+                v = e & (a.V - 1);
+            }
+            C v0, v1;
+            int64_t gp;
+            if (a.mode == 0) {
+                const int cl = lpo >> a.lg_len, m = lpo & (a.len - 1);  // m even in the contiguous case
+                const int c = c0 + cl;
+                if (a.contiguous) {  // the pair is (m, m + 1) of class c
+                    const int row = v << a.lg_nlt;
+                    v0 = sm[row + cl + (m << a.lg_Gt)];
+                    v1 = sm[row + cl + ((m + 1) << a.lg_Gt)];
+                    if (c != 0) {
+                        if (m != 0) v0 = cmul(v0, dirw<DIR>(tw[c * m]));
+                        v1 = cmul(v1, dirw<DIR>(tw[c * (m + 1)]));
+                    }
+                } else {  // the pair is vectors (v, v + 1) of one output position
+                    const int base = ((cl + (m << a.lg_Gt)) << a.lg_V) + v;
+                    v0 = sm[base];
+                    v1 = sm[base + 1];
+                    if (c != 0 && m != 0) {
+                        const C w = dirw<DIR>(tw[c * m]);
+                        v0 = cmul(v0, w);
+                        v1 = cmul(v1, w);
+                    }
+                }
+                gp = ((int64_t)c << a.lg_len) + m;
+            } else {
+                v0 = sm[e];
+                v1 = sm[e + 1];
+                gp = c0 + (lpo & (a.Gt - 1)) + ((int64_t)(lpo >> a.lg_Gt) << a.lg_G);
+            }
+            if (a.scale != 1.0) {
+                v0 = cscale(v0, scale);
+                v1 = cscale(v1, scale);
+            }
+            const int64_t g = a.contiguous ? gbase + (int64_t)v * a.nl + gp : gbase + gp * a.inner + v;
+            *reinterpret_cast<float4 *>(dst + g) = make_float4(v0.x, v0.y, v1.x, v1.y);
+        }
+        __syncthreads();
+        return;
+    }
     for (int e = tid; e < a.tile; e += nt) {
         int lpo, v;  // tile output position and vector
         if (a.contiguous) {
