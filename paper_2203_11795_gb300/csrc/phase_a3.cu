@@ -229,7 +229,7 @@ template <int N> __device__ __forceinline__ void consumer_sync() { asm volatile(
 // (the row swizzle makes the stage-2 reads of the landed block conflict-free).
 template <class K>
 __device__ __forceinline__ int x2_index(int b, int k2, int s2) {
-    constexpr int sig = 16 / K::P2 > 1 ? 16 / K::P2 : 1;
+    constexpr int sig = 16 / K::P2 > 1 ? 16 / K::P2 : 2;  // even, so k2 pairs stay adjacent
     const int sw = (s2 * sig) & (K::L2 - 1) & 15;
     return b * K::N2 + K::L2 * s2 + (k2 ^ sw);
 }
@@ -765,9 +765,13 @@ cudaError_t prepare_k(int n0, int n1, int *grids) {
 //                   two input buffers and a work buffer, 1 CTA/SM
 //   1024^3, p = 8^3: L = 128, rows 128 = 8 x 16, axis 1 = 8 x 16, axis 0 = 8 x 16, W = 4;
 //                   64 KB tiles, 512 consumer threads, 1 CTA/SM (residue units of 128 MiB: two kernels)
+//   1024^3, p = 16^3: L = 64, rows 64 = 8 x 8, axis 1 = 8 x 8, axis 0 = 8 x 8, W = 16; 64 KB tiles,
+//                   512 consumer threads, 1 CTA/SM; residue units of 32 MiB, so the ring (3 units)
+//                   is meant to stay in L2
 using K512p8 = Cfg<512, 8, 8, 8, 8, 64, 8, 8, 2, 2, true, false>;
 using K512p4 = Cfg<512, 4, 8, 8, 16, 128, 8, 4, 1, 2, true>;
 using K1024p8 = Cfg<1024, 8, 8, 8, 16, 128, 8, 4, 1, 2, true, true, 512>;
+using K1024p16 = Cfg<1024, 16, 8, 8, 8, 64, 8, 16, 1, 2, true, true, 512>;
 
 template <int DIR, bool PREP>
 cudaError_t dispatch(int which, const Phase3Launch *l, cudaStream_t st, int n0, int n1, int *grid, size_t *smem) {
@@ -781,6 +785,9 @@ cudaError_t dispatch(int which, const Phase3Launch *l, cudaStream_t st, int n0, 
         case 2:
             if (smem) *smem = pipe_smem_bytes<K1024p8>(n0, n1);
             return PREP ? prepare_k<K1024p8, DIR>(n0, n1, grid) : launch_k<K1024p8, DIR>(*l, st);
+        case 3:
+            if (smem) *smem = pipe_smem_bytes<K1024p16>(n0, n1);
+            return PREP ? prepare_k<K1024p16, DIR>(n0, n1, grid) : launch_k<K1024p16, DIR>(*l, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -813,6 +820,10 @@ int phase_a3_select(int d, const int64_t *n, const int64_t *p, int is_double, Ph
     if (matches<K1024p8>(n, p)) {
         fill<K1024p8>(*info);
         return 2;
+    }
+    if (matches<K1024p16>(n, p)) {
+        fill<K1024p16>(*info);
+        return 3;
     }
     return -1;
 }

@@ -212,7 +212,7 @@ def test_full_size_2d_16384(fftu, p):
     assert emax <= tolerance(np.complex64, x.size)
 
 
-@pytest.mark.parametrize("p", [(8, 8, 8), (4, 4, 4)], ids=["p8", "p4"])
+@pytest.mark.parametrize("p", [(8, 8, 8), (4, 4, 4), (16, 16, 16)], ids=["p8", "p4", "p16"])
 def test_full_size_1024_sampled(fftu, p):
     """1024^3 complex64: forward at sampled outputs (direct O(N) sums of eq. dftd), round trip
     and Parseval over the whole array."""
