@@ -91,7 +91,7 @@ struct Step {
 
 // Residue units up to this size run phase A as one persistent kernel whose
 // scratch ring (kRingSlots units) is meant to stay resident in L2.
-constexpr int64_t kRingUnitMaxBytes = 16ll << 20;
+constexpr int64_t kRingUnitMaxBytes = 32ll << 20;
 constexpr int kRingSlots = 3;
 constexpr int kRingLag = 1;  // stage 2 of unit u follows stage 1 of unit u + kRingLag (needs kRingLag < kRingSlots)
 constexpr long long kSpinLimitNs = 2000000000ll;
