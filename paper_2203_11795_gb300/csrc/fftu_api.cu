@@ -89,8 +89,10 @@ struct Step {
     Phase3Launch a3;
 };
 
-// Residue units up to this size run phase A as one persistent kernel whose
-// scratch ring (kRingSlots units) is meant to stay resident in L2.
+// Residue units up to this size run phase A as one persistent kernel through a
+// scratch ring of kRingSlots units.  Rings up to 48 MiB (16 MiB units, e.g. 512^3 at
+// p = 8^3) stay in L2; a 96 MiB ring (1024^3 at p = 16^3) partly spills to HBM and
+// is still faster than the two-kernel schedule.
 constexpr int64_t kRingUnitMaxBytes = 32ll << 20;
 constexpr int kRingSlots = 3;
 constexpr int kRingLag = 1;  // stage 2 of unit u follows stage 1 of unit u + kRingLag (needs kRingLag < kRingSlots)
