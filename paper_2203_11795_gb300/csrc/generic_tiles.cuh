@@ -488,7 +488,11 @@ __device__ __forceinline__ void phaseb_tile(const PhaseBFused &b, int64_t t, C *
         base += (rem & (b.L[l] - 1)) * b.stride[l];
         rem >>= b.lg_L[l];
     }
-    for (int e = tid; e < total; e += nt) {
+    // complex64 with Mt >= 2: elements mt and mt + 1 are adjacent along the last axis (stride 1),
+    // so loads and stores go in 16-byte pairs with one index computation per pair
+    const bool pairs = sizeof(C) == 8 && b.Mt >= 2;
+    const int step = pairs ? 2 : 1;
+    for (int e = tid * step; e < total; e += nt * step) {
         const int mt = e & (b.Mt - 1);
         int sf = e >> b.lg_Mt;
         int64_t g = base + (int64_t)mt * b.stride[d - 1];
@@ -497,7 +501,10 @@ __device__ __forceinline__ void phaseb_tile(const PhaseBFused &b, int64_t t, C *
             sf >>= b.lg_p[l];
             g += (int64_t)sl * b.L[l] * b.stride[l];
         }
-        async_copy(sm + e, data + g);
+        if (pairs)
+            async_copy_pair(reinterpret_cast<float2 *>(sm + e), reinterpret_cast<const float2 *>(data + g));
+        else
+            async_copy(sm + e, data + g);
     }
     async_copy_wait();
     __syncthreads();
@@ -514,7 +521,7 @@ __device__ __forceinline__ void phaseb_tile(const PhaseBFused &b, int64_t t, C *
         __syncthreads();
     }
     const Rl scale = (Rl)b.scale;
-    for (int e = tid; e < total; e += nt) {
+    for (int e = tid * step; e < total; e += nt * step) {
         const int mt = e & (b.Mt - 1);
         int sf = e >> b.lg_Mt;
         int64_t g = base + (int64_t)mt * b.stride[d - 1];
@@ -525,7 +532,13 @@ __device__ __forceinline__ void phaseb_tile(const PhaseBFused &b, int64_t t, C *
         }
         C v = sm[e];
         if (b.scale != 1.0) v = cscale(v, scale);
-        data[g] = v;
+        if (pairs) {
+            C w = sm[e + 1];
+            if (b.scale != 1.0) w = cscale(w, scale);
+            *reinterpret_cast<float4 *>(data + g) = make_float4(v.x, v.y, w.x, w.y);
+        } else {
+            data[g] = v;
+        }
     }
     __syncthreads();
 }
