@@ -171,7 +171,7 @@ fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPa
     } else {  // long line: a tile takes Gt of the G classes (runs of Gt along the line, or V across it)
         V = a.contiguous ? 1 : (inner < (is_double ? 4 : 8) ? inner : (is_double ? 4 : 8));
         while (V > 1 && a.len * V > maxtile) V /= 2;  // one sub-FFT of every vector must fit the tile
-        Gt = maxtile / (a.len * V);
+        Gt = (target < maxtile ? target : maxtile) / (a.len * V);  // classes per tile, up to the tile target
         if (Gt < 1) Gt = 1;
         if (Gt > a.G) Gt = a.G;
     }
