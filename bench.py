@@ -568,7 +568,9 @@ def run_serving(fftu, args, local):
     alg = sum(4 * math.prod(meta[c["tag"]][0]) * (16 if meta[c["tag"]][1] else 8) for c in timed)
     moved = sum(2 * math.prod(meta[c["tag"]][0]) * (16 if meta[c["tag"]][1] else 8) for c in timed)
     d = {k: stats1[k] - stats0[k] for k in ("batches", "graph_replays", "direct_launches", "kernel_launches",
-                                              "rejected", "evictions")}
+                                              "rejected", "evictions", "instance_creations", "creation_s")}
+    d["max_launch_ms"] = stats1["max_launch_s"] * 1e3
+    d["max_loop_gap_ms"] = stats1["max_loop_gap_s"] * 1e3
     per_class = {}
     for shape in SERVE_SHAPES:
         for c128 in (False, True):

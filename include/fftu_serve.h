@@ -77,6 +77,13 @@ typedef struct {
     int64_t bytes_in_use, peak_bytes, budget_bytes;
     int64_t evictions;
     int64_t bytes_h2d, bytes_d2h;   /* request bytes copied each way */
+    int64_t instance_creations;     /* resident batch instances created (device buffers, plan or batch, graph) */
+    double creation_s;              /* host time the server thread spent creating them */
+    double max_launch_s;            /* longest host time of issuing one launch (copies, graph, kernels) */
+    double max_loop_gap_s;          /* longest time between two passes of the server loop */
+    int last_cuda_error;            /* last CUDA error the server met (cudaError_t; 0 = none) */
+    int last_error_site;            /* where: 1 input copy, 2 transform launch, 3 output copy, 4 event record,
+                                       5 completion event, 6 graph build, 7 graph replay */
 } fftu_server_stats;
 
 /* Start a server (cfg may be NULL = defaults).  FFTU_ERR_ARG on an invalid config. */

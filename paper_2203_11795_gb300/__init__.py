@@ -85,7 +85,9 @@ class fftu_server_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "submitted", "completed", "rejected", "batches", "graph_replays", "graph_builds", "direct_launches",
         "kernel_launches", "instances", "plans", "bytes_in_use", "peak_bytes", "budget_bytes", "evictions",
-        "bytes_h2d", "bytes_d2h")]
+        "bytes_h2d", "bytes_d2h", "instance_creations")] + [
+        ("creation_s", ctypes.c_double), ("max_launch_s", ctypes.c_double), ("max_loop_gap_s", ctypes.c_double),
+        ("last_cuda_error", ctypes.c_int), ("last_error_site", ctypes.c_int)]
 
 
 def _load_library() -> ctypes.CDLL:

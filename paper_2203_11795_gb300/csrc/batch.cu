@@ -150,7 +150,10 @@ __global__ void wait_probe_kernel(unsigned *words, long long limit_ns) {
 
 template <typename C, int DIR>
 cudaError_t batch_setup(size_t smem, int threads, int *grid) {
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel<C, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // The limit is a property of the kernel, shared by every batch: set it to the largest tile any
+    // batch can use, never to this batch's (a later, smaller batch would make this one's launches fail).
+    if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<C, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);

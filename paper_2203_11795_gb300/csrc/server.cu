@@ -72,6 +72,7 @@ struct Instance {
     cudaGraphExec_t gexec = nullptr;
     std::vector<cudaGraphNode_t> h2d, d2h;
     bool graph_failed = false;
+    bool building = false;             // a graph for it is being built off the server thread
     int piece_mib = 0;
     bool busy = false;
     std::vector<Req> reqs;
@@ -114,6 +115,16 @@ struct fftu_server_st {
 
     std::mutex stats_mu;
     fftu_server_stats stats;
+
+    // graph builder thread: instantiating a graph takes milliseconds, so it runs beside the server
+    // thread, which keeps dispatching (plain copies) until the graph arrives
+    std::thread builder;
+    std::mutex b_mu;
+    std::condition_variable b_cv;
+    std::deque<void *> b_jobs;  // GraphBuild *
+    std::vector<void *> b_done;
+    bool b_stop = false;
+    cudaStream_t b_stream = nullptr;
 
     std::map<Key, std::unique_ptr<KeyState>> keys;  // server thread only
     size_t used = 0;
@@ -177,6 +188,12 @@ int plan_launches(fftu_handle h) {
     return info.launches_phase_a + info.launches_phase_b;
 }
 
+void note_cuda_error(fftu_server_st *S, cudaError_t e, int site) {
+    std::lock_guard<std::mutex> lk(S->stats_mu);
+    S->stats.last_cuda_error = (int)e;
+    S->stats.last_error_site = site;
+}
+
 void destroy_instance(fftu_server_st *S, Instance *in) {
     if (in->gexec) cudaGraphExecDestroy(in->gexec);
     if (in->graph) cudaGraphDestroy(in->graph);
@@ -197,7 +214,7 @@ bool make_room(fftu_server_st *S, size_t need, const KeyState *keep) {
         for (auto &kv : S->keys) {
             KeyState *ks = kv.second.get();
             for (auto &in : ks->inst)
-                if (!in->busy && (!victim || in->last_used < victim->last_used)) {
+                if (!in->busy && !in->building && (!victim || in->last_used < victim->last_used)) {
                     victim = in.get();
                     vks = ks;
                 }
@@ -241,8 +258,20 @@ fftu_status ensure_plan(fftu_server_st *S, KeyState *ks) {
     return FFTU_OK;
 }
 
+Instance *new_instance_impl(fftu_server_st *S, KeyState *ks, int k, bool large, fftu_status *err);
+
 // A new instance of k requests of ks; nullptr when the budget cannot hold it right now.
 Instance *new_instance(fftu_server_st *S, KeyState *ks, int k, bool large, fftu_status *err) {
+    const double t0 = S->now();
+    Instance *in = new_instance_impl(S, ks, k, large, err);
+    const double dt = S->now() - t0;
+    std::lock_guard<std::mutex> lk(S->stats_mu);
+    S->stats.creation_s += dt;
+    if (in) S->stats.instance_creations++;
+    return in;
+}
+
+Instance *new_instance_impl(fftu_server_st *S, KeyState *ks, int k, bool large, fftu_status *err) {
     *err = FFTU_OK;
     auto in = std::make_unique<Instance>();
     in->ks = ks;
@@ -330,53 +359,72 @@ int pieces(const Instance *in, size_t bytes) {
     return (int)((bytes + pb - 1) / pb);
 }
 
-bool build_graph(Instance *in) {
+// A graph of one instance's launch (copies in, transform, copies out), built off the server thread.
+struct GraphBuild {
+    Instance *in = nullptr;
+    std::vector<const void *> hin;  // host addresses the copy nodes start with (re-pointed at each replay)
+    std::vector<void *> hout;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<cudaGraphNode_t> h2d, d2h;
+    cudaError_t error = cudaSuccess;
+    bool ok = false;
+};
+
+// Capture the transform on `cs` (a stream of the builder's own) and instantiate the graph.
+void build_graph(GraphBuild &b, cudaStream_t cs) {
+    Instance *in = b.in;
     const size_t bytes = (size_t)in->ks->N * in->ks->esize;
     const size_t kCopyPiece = piece_bytes(in, bytes);
     const int c = pieces(in, bytes);
     cudaGraph_t g = nullptr, child = nullptr;
-    if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+        b.error = cudaGetLastError();
+        return;
+    }
     bool ok = true;
-    in->h2d.assign((size_t)in->k * c, nullptr);
-    in->d2h.assign((size_t)in->k * c, nullptr);
+    b.h2d.assign((size_t)in->k * c, nullptr);
+    b.d2h.assign((size_t)in->k * c, nullptr);
     for (int i = 0; ok && i < in->k; ++i)
         for (int j = 0; ok && j < c; ++j) {
             const size_t off = (size_t)j * kCopyPiece, len = std::min(kCopyPiece, bytes - off);
-            cudaGraphNode_t *prev = j > 0 ? &in->h2d[(size_t)i * c + j - 1] : nullptr;
-            ok = cudaGraphAddMemcpyNode1D(&in->h2d[(size_t)i * c + j], g, prev, prev ? 1 : 0,
+            cudaGraphNode_t *prev = j > 0 ? &b.h2d[(size_t)i * c + j - 1] : nullptr;
+            ok = cudaGraphAddMemcpyNode1D(&b.h2d[(size_t)i * c + j], g, prev, prev ? 1 : 0,
                                           static_cast<char *>(in->in_slot(i)) + off,
-                                          static_cast<const char *>(in->reqs[i].r.in) + off, len,
+                                          static_cast<const char *>(b.hin[i]) + off, len,
                                           cudaMemcpyHostToDevice) == cudaSuccess;
         }
     if (ok) {
-        ok = cudaStreamBeginCapture(in->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
         if (ok) {
-            const fftu_status st = compute(in, in->stream);
-            ok = cudaStreamEndCapture(in->stream, &child) == cudaSuccess && st == FFTU_OK && child;
+            const fftu_status st = compute(in, cs);
+            ok = cudaStreamEndCapture(cs, &child) == cudaSuccess && st == FFTU_OK && child;
         }
     }
     cudaGraphNode_t cn = nullptr;
-    if (ok) ok = cudaGraphAddChildGraphNode(&cn, g, in->h2d.data(), in->h2d.size(), child) == cudaSuccess;
+    if (ok) ok = cudaGraphAddChildGraphNode(&cn, g, b.h2d.data(), b.h2d.size(), child) == cudaSuccess;
     for (int i = 0; ok && i < in->k; ++i)
         for (int j = 0; ok && j < c; ++j) {
             const size_t off = (size_t)j * kCopyPiece, len = std::min(kCopyPiece, bytes - off);
-            cudaGraphNode_t *prev = j > 0 ? &in->d2h[(size_t)i * c + j - 1] : &cn;
-            ok = cudaGraphAddMemcpyNode1D(&in->d2h[(size_t)i * c + j], g, prev, 1,
-                                          static_cast<char *>(in->reqs[i].r.out) + off,
+            cudaGraphNode_t *prev = j > 0 ? &b.d2h[(size_t)i * c + j - 1] : &cn;
+            ok = cudaGraphAddMemcpyNode1D(&b.d2h[(size_t)i * c + j], g, prev, 1,
+                                          static_cast<char *>(b.hout[i]) + off,
                                           static_cast<const char *>(in->out_slot(i)) + off, len,
                                           cudaMemcpyDeviceToHost) == cudaSuccess;
         }
     if (child) cudaGraphDestroy(child);
-    if (ok) ok = cudaGraphInstantiate(&in->gexec, g, 0) == cudaSuccess;
+    if (ok) ok = cudaGraphInstantiate(&b.gexec, g, 0) == cudaSuccess;
+    // upload now, on the builder's stream, so that the first replay does not pay for it
+    if (ok) ok = cudaGraphUpload(b.gexec, cs) == cudaSuccess && cudaStreamSynchronize(cs) == cudaSuccess;
     if (!ok) {
-        cudaGetLastError();
-        if (in->gexec) cudaGraphExecDestroy(in->gexec);
-        in->gexec = nullptr;
+        b.error = cudaGetLastError();
+        if (b.gexec) cudaGraphExecDestroy(b.gexec);
+        b.gexec = nullptr;
         cudaGraphDestroy(g);
-        return false;
+        return;
     }
-    in->graph = g;
-    return true;
+    b.graph = g;
+    b.ok = true;
 }
 
 bool page_locked(const void *p) {
@@ -393,17 +441,36 @@ void launch(fftu_server_st *S, Instance *in) {
     const size_t bytes = (size_t)in->ks->N * in->ks->esize;
     in->busy = true;
     in->t_start = S->now();
+    struct LaunchTimer {  // longest host time of one launch, in the stats
+        fftu_server_st *S;
+        double t0;
+        ~LaunchTimer() {
+            const double dt = S->now() - t0;
+            std::lock_guard<std::mutex> lk(S->stats_mu);
+            if (dt > S->stats.max_launch_s) S->stats.max_launch_s = dt;
+        }
+    } timer{S, in->t_start};
     in->last_used = ++S->tick;
     in->ks->last_used = S->tick;
     bool locked = S->cfg.use_graphs && !in->graph_failed;
     for (int i = 0; locked && i < in->k; ++i) locked = page_locked(in->reqs[i].r.in) && page_locked(in->reqs[i].r.out);
     fftu_status st = FFTU_OK;
-    bool graphed = false, built = false;
-    if (locked) {
-        if (!in->gexec) {
-            built = build_graph(in);
-            if (!built) in->graph_failed = true;
+    bool graphed = false;
+    if (locked && !in->gexec && !in->building) {  // first use with page-locked buffers: build a graph
+        auto *job = new GraphBuild();
+        job->in = in;
+        for (int i = 0; i < in->k; ++i) {
+            job->hin.push_back(in->reqs[i].r.in);
+            job->hout.push_back(in->reqs[i].r.out);
         }
+        in->building = true;
+        {
+            std::lock_guard<std::mutex> lk(S->b_mu);
+            S->b_jobs.push_back(job);
+        }
+        S->b_cv.notify_one();
+    }
+    if (locked) {
         if (in->gexec) {
             bool ok = true;
             const size_t kCopyPiece = piece_bytes(in, bytes);
@@ -425,30 +492,46 @@ void launch(fftu_server_st *S, Instance *in) {
             if (ok) {
                 graphed = true;
             } else {
-                cudaGetLastError();
+                note_cuda_error(S, cudaGetLastError(), 7);
                 in->graph_failed = true;
             }
         }
     }
     if (!graphed) {
-        for (int i = 0; st == FFTU_OK && i < in->k; ++i)
-            if (cudaMemcpyAsync(in->in_slot(i), in->reqs[i].r.in, bytes, cudaMemcpyHostToDevice, in->stream) !=
-                cudaSuccess)
+        for (int i = 0; st == FFTU_OK && i < in->k; ++i) {
+            const cudaError_t e = cudaMemcpyAsync(in->in_slot(i), in->reqs[i].r.in, bytes, cudaMemcpyHostToDevice,
+                                                  in->stream);
+            if (e != cudaSuccess) {
+                note_cuda_error(S, e, 1);
                 st = FFTU_ERR_CUDA;
-        if (st == FFTU_OK) st = compute(in, in->stream);
-        for (int i = 0; st == FFTU_OK && i < in->k; ++i)
-            if (cudaMemcpyAsync(in->reqs[i].r.out, in->out_slot(i), bytes, cudaMemcpyDeviceToHost, in->stream) !=
-                cudaSuccess)
+            }
+        }
+        if (st == FFTU_OK) {
+            st = compute(in, in->stream);
+            if (st != FFTU_OK) note_cuda_error(S, cudaPeekAtLastError(), 2);
+        }
+        for (int i = 0; st == FFTU_OK && i < in->k; ++i) {
+            const cudaError_t e = cudaMemcpyAsync(in->reqs[i].r.out, in->out_slot(i), bytes, cudaMemcpyDeviceToHost,
+                                                  in->stream);
+            if (e != cudaSuccess) {
+                note_cuda_error(S, e, 3);
                 st = FFTU_ERR_CUDA;
+            }
+        }
     }
-    if (st == FFTU_OK && cudaEventRecord(in->done, in->stream) != cudaSuccess) st = FFTU_ERR_CUDA;
+    if (st == FFTU_OK) {
+        const cudaError_t e = cudaEventRecord(in->done, in->stream);
+        if (e != cudaSuccess) {
+            note_cuda_error(S, e, 4);
+            st = FFTU_ERR_CUDA;
+        }
+    }
     {
         std::lock_guard<std::mutex> lk(S->stats_mu);
         S->stats.batches++;
         S->stats.kernel_launches += in->launches;
         if (graphed) S->stats.graph_replays++;
         else S->stats.direct_launches++;
-        if (built) S->stats.graph_builds++;
         S->stats.bytes_h2d += (int64_t)(bytes * in->k);
         S->stats.bytes_d2h += (int64_t)(bytes * in->k);
     }
@@ -470,7 +553,10 @@ bool reap(fftu_server_st *S) {
             const cudaError_t e = cudaEventQuery(in->done);
             if (e == cudaErrorNotReady) continue;
             int status = e == cudaSuccess ? FFTU_OK : FFTU_ERR_CUDA;
-            if (e != cudaSuccess) cudaGetLastError();
+            if (e != cudaSuccess) {
+                note_cuda_error(S, e, 5);
+                cudaGetLastError();
+            }
             for (auto &q : in->reqs) complete(S, q, status, in->k, in->t_start);
             in->reqs.clear();
             in->busy = false;
@@ -575,10 +661,62 @@ bool any_pending(fftu_server_st *S) {
     return false;
 }
 
+void builder_main(fftu_server_st *S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        GraphBuild *job = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->b_mu);
+            S->b_cv.wait(lk, [&] { return S->b_stop || !S->b_jobs.empty(); });
+            if (S->b_jobs.empty()) return;  // stopping
+            job = static_cast<GraphBuild *>(S->b_jobs.front());
+            S->b_jobs.pop_front();
+        }
+        build_graph(*job, S->b_stream);
+        std::lock_guard<std::mutex> lk(S->b_mu);
+        S->b_done.push_back(job);
+    }
+}
+
+// Attach graphs the builder has finished to their (idle or busy) instances.
+void collect_graphs(fftu_server_st *S) {
+    std::vector<void *> done;
+    {
+        std::lock_guard<std::mutex> lk(S->b_mu);
+        done.swap(S->b_done);
+    }
+    for (void *p : done) {
+        auto *b = static_cast<GraphBuild *>(p);
+        Instance *in = b->in;
+        in->building = false;
+        if (b->ok) {
+            in->graph = b->graph;
+            in->gexec = b->gexec;
+            in->h2d = std::move(b->h2d);
+            in->d2h = std::move(b->d2h);
+            std::lock_guard<std::mutex> lk(S->stats_mu);
+            S->stats.graph_builds++;
+        } else {
+            in->graph_failed = true;
+            note_cuda_error(S, b->error, 6);
+        }
+        delete b;
+    }
+}
+
 void server_main(fftu_server_st *S) {
     cudaSetDevice(S->device);
     std::deque<Req> local;
+    double last = S->now();
     for (;;) {
+        {
+            const double now = S->now();
+            if (now - last > S->stats.max_loop_gap_s) {
+                std::lock_guard<std::mutex> lk(S->stats_mu);
+                S->stats.max_loop_gap_s = now - last;
+            }
+            last = now;
+        }
         {
             std::unique_lock<std::mutex> lk(S->in_mu);
             if (S->inbox.empty() && !S->stop.load() && !any_busy(S) && !any_pending(S))
@@ -586,6 +724,7 @@ void server_main(fftu_server_st *S) {
             local.swap(S->inbox);
         }
         intake(S, local);
+        collect_graphs(S);
         const bool reaped = reap(S);
         const bool started = dispatch(S);
         if (S->stop.load() && !any_busy(S)) break;
@@ -598,6 +737,24 @@ void server_main(fftu_server_st *S) {
         std::lock_guard<std::mutex> lk(S->in_mu);
         for (auto &q : S->inbox) complete(S, q, FFTU_ERR_ARG, 0, 0);
         S->inbox.clear();
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->b_mu);
+        S->b_stop = true;
+    }
+    S->b_cv.notify_all();
+    if (S->builder.joinable()) S->builder.join();
+    {  // graphs that finished after the last collection, and jobs never started
+        std::lock_guard<std::mutex> lk(S->b_mu);
+        for (void *p : S->b_done) {
+            auto *b = static_cast<GraphBuild *>(p);
+            if (b->gexec) cudaGraphExecDestroy(b->gexec);
+            if (b->graph) cudaGraphDestroy(b->graph);
+            delete b;
+        }
+        for (void *p : S->b_jobs) delete static_cast<GraphBuild *>(p);
+        S->b_done.clear();
+        S->b_jobs.clear();
     }
     for (auto &kv : S->keys) {
         for (auto &in : kv.second->inst) destroy_instance(S, in.get());
@@ -665,6 +822,13 @@ fftu_status fftu_server_create(const fftu_server_config *cfg, fftu_server *out) 
         S->streams.push_back(s);
     }
     S->split = c.streams >= 2 ? c.streams / 2 : c.streams;
+    if (cudaStreamCreateWithFlags(&S->b_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        for (auto x : S->streams) cudaStreamDestroy(x);
+        delete S;
+        return FFTU_ERR_CUDA;
+    }
+    S->builder = std::thread(builder_main, S);
     S->thread = std::thread(server_main, S);
     *out = S;
     return FFTU_OK;
@@ -732,6 +896,7 @@ fftu_status fftu_server_destroy(fftu_server S) {
     S->in_cv.notify_one();
     if (S->thread.joinable()) S->thread.join();
     for (auto s : S->streams) cudaStreamDestroy(s);
+    if (S->b_stream) cudaStreamDestroy(S->b_stream);
     delete S;
     return FFTU_OK;
 }

@@ -93,3 +93,29 @@ def test_batch_rejects_mixed_plans(fftu):
         with pytest.raises(fftu.FFTUError) as ei:
             fftu.fftu_batch_create([longline.handle])
         assert ei.value.status == 3
+
+
+def test_batch_after_smaller_batch_is_created(fftu):
+    """The kernel's shared-memory limit is shared by all batches: creating a batch with smaller
+    tiles must not break a batch with larger ones (found with the serving loop)."""
+    import torch
+    big_shapes = [(128, 128, 128), (64, 128, 32)]
+    xs = [torch.from_numpy(complex_uniform(300 + i, s, dtype=np.complex64)).cuda() for i, s in enumerate(big_shapes)]
+    outs = [torch.empty_like(x) for x in xs]
+    plans = [fftu.Plan(s, None) for s in big_shapes]
+    small = fftu.Plan((8, 8), None)
+    big = fftu.fftu_batch_create([p.handle for p in plans])
+    little = fftu.fftu_batch_create([small.handle])
+    try:
+        stream = torch.cuda.current_stream()
+        fftu.fftu_batch_exec(big, [x.data_ptr() for x in xs], [o.data_ptr() for o in outs], stream.cuda_stream)
+        torch.cuda.synchronize()
+        fftu.fftu_batch_check_status(big)
+    finally:
+        fftu.fftu_batch_destroy(little)
+        fftu.fftu_batch_destroy(big)
+        for p in plans + [small]:
+            p.close()
+    for x, y in zip(xs, outs):
+        ref = oracle.fftn(x.cpu().numpy().astype(np.complex128))
+        assert oracle.rel_l2(y.cpu().numpy(), ref) <= 1e-5 * math.log2(x.numel())

@@ -303,3 +303,24 @@ def test_tile_and_radix_options(fftu, case, tile, radix, inverse):
         plan.check_device_status()
     ref = oracle.fftn(x.astype(np.complex128), inverse=inverse)
     assert oracle.rel_l2(y.cpu().numpy(), ref) <= tolerance(dt, x.size)
+
+
+def test_fused_plan_after_smaller_plan_on_same_kernel(fftu):
+    """512^3 and 512 x 256 x 512 (p = 8 x 4 x 8) use the same fused phase-A kernel with different
+    shared-memory sizes; making the second plan must not break the first."""
+    import torch
+    x = complex_uniform(4242, (512, 512, 512), dtype=np.complex64)
+    xt = torch.from_numpy(x).cuda()
+    with fftu.Plan(x.shape, (8, 8, 8)) as a:
+        assert a.info["launches_phase_a"] == 1           # the fused ring kernel
+        with fftu.Plan((512, 256, 512), (8, 4, 8)) as b:
+            assert b.info["launches_phase_a"] == 1
+            yb = b.exec(torch.from_numpy(complex_uniform(4243, (512, 256, 512), dtype=np.complex64)).cuda())
+            y = a.exec(xt)
+            torch.cuda.synchronize()
+            a.check_device_status()
+            b.check_device_status()
+    idx = [(0, 0, 0), (1, 2, 3), (511, 77, 300), (256, 256, 256)]
+    ref = oracle.dft_points(x.astype(np.complex128), idx)
+    got = np.array([y[i].item() for i in idx])
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-4

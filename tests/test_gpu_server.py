@@ -38,8 +38,9 @@ def make_mix(count, seed, shapes=SHAPES, c128_share=0.25):
     return reqs
 
 
-def run_server(fftu, reqs, pinned=True, poll_timeout=60.0, **cfg):
-    """Submit every request, wait for all completions; returns (outputs by tag, completions, stats)."""
+def run_server(fftu, reqs, pinned=True, poll_timeout=60.0, passes=1, **cfg):
+    """Submit every request (passes times, waiting for all completions after each pass); returns
+    (outputs by tag, completions of the last pass, stats)."""
     import torch
     bufs = {}
     for shape, dt, inverse, seed in reqs:  # every buffer first, so that the submissions come in a burst
@@ -50,13 +51,14 @@ def run_server(fftu, reqs, pinned=True, poll_timeout=60.0, **cfg):
         bufs[seed] = (x, y)
     s = fftu.fftu_server_create(**cfg)
     try:
-        for shape, dt, inverse, seed in reqs:
-            x, y = bufs[seed]
-            code = fftu.FFTU_C128 if dt == np.complex128 else fftu.FFTU_C64
-            fftu.fftu_server_submit(s, shape, code, fftu.FFTU_INVERSE if inverse else fftu.FFTU_FORWARD,
-                                    x.data_ptr(), y.data_ptr(), seed)
-        fftu.fftu_server_drain(s, poll_timeout)
-        done = fftu.fftu_server_poll(s, 4096)
+        for _ in range(passes):
+            for shape, dt, inverse, seed in reqs:
+                x, y = bufs[seed]
+                code = fftu.FFTU_C128 if dt == np.complex128 else fftu.FFTU_C64
+                fftu.fftu_server_submit(s, shape, code, fftu.FFTU_INVERSE if inverse else fftu.FFTU_FORWARD,
+                                        x.data_ptr(), y.data_ptr(), seed)
+            fftu.fftu_server_drain(s, poll_timeout)
+            done = fftu.fftu_server_poll(s, 4096)
         stats = fftu.fftu_server_stats_get(s)
     finally:
         fftu.fftu_server_destroy(s)
@@ -75,10 +77,12 @@ def check_against_oracle(reqs, outs, done):
 
 def test_mixed_stream_matches_oracle(fftu):
     reqs = make_mix(60, seed=1)
-    outs, done, stats = run_server(fftu, reqs, max_batch=16, max_inflight=1)
+    outs, done, stats = run_server(fftu, reqs, max_batch=16, max_inflight=1, passes=2)
     check_against_oracle(reqs, outs, done)
-    assert stats["completed"] == 60 and stats["rejected"] == 0
-    assert stats["graph_replays"] > 0 and stats["batches"] < 60  # batched and graph-replayed
+    assert stats["completed"] == 120 and stats["rejected"] == 0
+    assert stats["batches"] < 120                                     # batched
+    assert stats["graph_builds"] > 0 and stats["graph_replays"] > 0   # graphs built while idle, then replayed
+    assert stats["graph_replays"] + stats["direct_launches"] == stats["batches"]
     for c in done:
         assert c["submit_s"] <= c["start_s"] <= c["done_s"]
 
