@@ -31,6 +31,7 @@ if ROOT not in sys.path:
 
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 8000.0  # the nominal HBM3e figure the target is also quoted against
+FP64_PEAK_GFLOPS = 1250.0  # GB300 FP64 nominal: complex128 transforms are bound by FP64 arithmetic
 METRIC = "3D FFT HBM GB/s & % roofline at 512^3 c64; mixed-request p50/p99 latency"
 METRIC_DETAIL = ("value: algorithmic HBM GB/s, B_alg = 4 N b bytes per transform (b = element size), "
                  "one forward + one inverse transform per step; the mixed-request p50/p99 latency is the "
@@ -391,6 +392,14 @@ def run_ours(args):
                     "phase_ms": {"phase_a": ta, "phase_b": tb},
                     "phase_frac": {"phase_a": half / (ta * 1e-3) / 1e9 / peak,
                                    "phase_b": half / (tb * 1e-3) / 1e9 / peak}}
+        if esize == 16:
+            # complex128: FP64 arithmetic, not HBM, bounds the path on GB300 (1.25 TFLOP/s FP64 against
+            # 6.8 TB/s; about 5 log2 N flops per element per transform need 16 B of traffic per flop-pass)
+            gf = 2 * 5 * N * math.log2(N) / (ms_per_step * 1e-3) / 1e9
+            roofline = {"bound": "alu", "achieved": gf, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                        "frac": gf / FP64_PEAK_GFLOPS, "traffic": None, "kernel": "whole step",
+                        "peak_source": "GB300 FP64 nominal (1.25 TFLOP/s); flops counted as 5 N log2 N per transform",
+                        "hbm": roofline}
         serving = None
         if not args.no_serve and world == 1 and tuple(shape) == (512, 512, 512):
             try:
