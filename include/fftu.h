@@ -159,7 +159,9 @@ typedef struct {
 fftu_status fftu_plan(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,
                       fftu_handle *out);
 
-/* fftu_plan with options (opts may be NULL = defaults).  With p == NULL and opts->tune != 0 the
+/* fftu_plan with options (opts may be NULL = defaults).  With p == NULL the plan takes the process's
+ * wisdom for the problem when there is some (from an earlier tuned plan or fftu_wisdom_import), else
+ * the default grid (the largest power of two up to 8 with p_l^2 | n_l, per axis).  With p == NULL and opts->tune != 0 the
  * planner measures, on scratch buffers it allocates for the duration (2 N elements), one coordinate at
  * a time: every candidate grid p_l = min(q, pmax_l), q = 1, 2, 4, ... (pmax_l: the largest power of two
  * with p_l^2 | n_l); then, for the fastest grid, the schedules (AUTO, GENERIC_A, GENERIC) unless

@@ -588,11 +588,13 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
             return FFTU_ERR_UNSUPPORTED;
         }
     int tuned = 0;
-    if (!p && opts && opts->tune) {
-        fftu_options base = *opts;
+    if (!p) {  // measured tuning on request; otherwise wisdom for this problem, if the process has any
+        fftu_options base;
+        std::memset(&base, 0, sizeof(base));
+        if (opts) base = *opts;
         base.schedule = sched;
         TuneChoice tc;
-        if (autotune(d, n, dtype, dir, base, &tc)) {
+        if (opts && opts->tune ? autotune(d, n, dtype, dir, base, &tc) : wisdom_lookup(d, n, dtype, dir, base, &tc)) {
             for (int l = 0; l < d; ++l) pp[l] = tc.p[l];
             sched = tc.schedule;
             if (tc.tile) tile = tc.tile;

@@ -120,6 +120,7 @@ struct TuneChoice {
     int schedule, tile, radix;
 };
 bool autotune(int d, const int64_t *n, fftu_dtype dtype, fftu_dir dir, const fftu_options &base, TuneChoice *t);
+bool wisdom_lookup(int d, const int64_t *n, fftu_dtype dtype, fftu_dir dir, const fftu_options &base, TuneChoice *t);
 
 // Set the calling thread's detail string returned by fftu_last_error().
 void record_error(const char *msg);

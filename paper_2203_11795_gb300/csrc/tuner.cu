@@ -84,21 +84,24 @@ float time_candidate(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype
 
 }  // namespace
 
+// The wisdom entry for the problem, if any (no measurement).
+bool wisdom_lookup(int d, const int64_t *n, fftu_dtype dtype, fftu_dir dir, const fftu_options &base, TuneChoice *t) {
+    const std::string key = wisdom_key(d, n, dtype, dir, base.schedule, base.precision);
+    std::lock_guard<std::mutex> lock(g_wisdom_mutex);
+    auto it = g_wisdom.find(key);
+    if (it == g_wisdom.end() || (int)it->second.p.size() != d) return false;
+    for (int l = 0; l < d; ++l) t->p[l] = it->second.p[l];
+    t->schedule = it->second.schedule ? it->second.schedule : base.schedule;
+    t->tile = it->second.tile ? it->second.tile : base.tile;
+    t->radix = it->second.radix ? it->second.radix : base.radix;
+    return true;
+}
+
 // Fills `t` (p, and schedule / tile / radix where the caller left them open); returns true when
 // tuning ran or wisdom answered, false when the caller should use the defaults.
 bool autotune(int d, const int64_t *n, fftu_dtype dtype, fftu_dir dir, const fftu_options &base, TuneChoice *t) {
     const std::string key = wisdom_key(d, n, dtype, dir, base.schedule, base.precision);
-    {
-        std::lock_guard<std::mutex> lock(g_wisdom_mutex);
-        auto it = g_wisdom.find(key);
-        if (it != g_wisdom.end() && (int)it->second.p.size() == d) {
-            for (int l = 0; l < d; ++l) t->p[l] = it->second.p[l];
-            t->schedule = it->second.schedule ? it->second.schedule : base.schedule;
-            t->tile = it->second.tile ? it->second.tile : base.tile;
-            t->radix = it->second.radix ? it->second.radix : base.radix;
-            return true;
-        }
-    }
+    if (wisdom_lookup(d, n, dtype, dir, base, t)) return true;
     int64_t N = 1, pmax[FFTU_MAX_DIMS];
     for (int l = 0; l < d; ++l) {
         N *= n[l];

@@ -22,6 +22,14 @@ def fftu():
     return f
 
 
+@pytest.fixture(autouse=True)
+def _clean_wisdom(fftu):
+    """Wisdom is process-wide and plain plans with p = NULL use it: leave none behind."""
+    fftu.fftu_wisdom_forget()
+    yield
+    fftu.fftu_wisdom_forget()
+
+
 def _key(shape, dtype_code, direction):
     import torch
     name = torch.cuda.get_device_name(0).replace(" ", "_")
@@ -72,7 +80,28 @@ def test_imported_wisdom_is_obeyed(fftu, tmp_path):
         out = plan.exec(t)
         torch.cuda.synchronize()
     assert oracle.rel_l2(out.cpu().numpy(), oracle.fftn(x.astype(np.complex128))) < 1e-4
-    # an untuned plan ignores wisdom and keeps the default grid
+    # a plain plan (no tuning requested) takes the same wisdom
     with fftu.Plan(shape, None, dtype=t.dtype) as plan:
-        assert plan.info["tuned"] == 0
+        assert plan.info["p"] == [2, 1, 4] and plan.info["tuned"] == 1
     fftu.fftu_wisdom_forget()
+
+
+def test_plain_plan_uses_wisdom(fftu, tmp_path):
+    """p = NULL without tuning takes the process's wisdom for the problem, else the default grid."""
+    import torch
+    shape = (64, 64, 64)
+    with fftu.Plan(shape, None) as plan:
+        assert plan.info["p"] == [8, 8, 8] and plan.info["tuned"] == 0
+    path = tmp_path / "w.txt"
+    path.write_text(f"fftu-wisdom-v2 {_key(shape, fftu.FFTU_C64, fftu.FFTU_FORWARD)} 4,2,4 0 2048 8\n")
+    fftu.fftu_wisdom_import(str(path))
+    x = complex_uniform(9, shape, dtype=np.complex64)
+    with fftu.Plan(shape, None) as plan:
+        info = plan.info
+        assert info["p"] == [4, 2, 4] and info["tuned"] == 1 and info["tile"] == 2048
+        y = plan.exec(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+    assert oracle.rel_l2(y.cpu().numpy(), oracle.fftn(x.astype(np.complex128))) < 1e-4
+    fftu.fftu_wisdom_forget()
+    with fftu.Plan(shape, None) as plan:
+        assert plan.info["p"] == [8, 8, 8]
