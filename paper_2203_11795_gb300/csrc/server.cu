@@ -55,6 +55,7 @@ struct Req {
 };
 
 struct KeyState;
+struct GraphBuild;
 
 struct Instance {
     KeyState *ks = nullptr;
@@ -121,8 +122,8 @@ struct fftu_server_st {
     std::thread builder;
     std::mutex b_mu;
     std::condition_variable b_cv;
-    std::deque<void *> b_jobs;  // GraphBuild *
-    std::vector<void *> b_done;
+    std::deque<GraphBuild *> b_jobs;
+    std::vector<GraphBuild *> b_done;
     bool b_stop = false;
     cudaStream_t b_stream = nullptr;
 
@@ -375,7 +376,7 @@ struct GraphBuild {
 void build_graph(GraphBuild &b, cudaStream_t cs) {
     Instance *in = b.in;
     const size_t bytes = (size_t)in->ks->N * in->ks->esize;
-    const size_t kCopyPiece = piece_bytes(in, bytes);
+    const size_t piece = piece_bytes(in, bytes);
     const int c = pieces(in, bytes);
     cudaGraph_t g = nullptr, child = nullptr;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) {
@@ -387,7 +388,7 @@ void build_graph(GraphBuild &b, cudaStream_t cs) {
     b.d2h.assign((size_t)in->k * c, nullptr);
     for (int i = 0; ok && i < in->k; ++i)
         for (int j = 0; ok && j < c; ++j) {
-            const size_t off = (size_t)j * kCopyPiece, len = std::min(kCopyPiece, bytes - off);
+            const size_t off = (size_t)j * piece, len = std::min(piece, bytes - off);
             cudaGraphNode_t *prev = j > 0 ? &b.h2d[(size_t)i * c + j - 1] : nullptr;
             ok = cudaGraphAddMemcpyNode1D(&b.h2d[(size_t)i * c + j], g, prev, prev ? 1 : 0,
                                           static_cast<char *>(in->in_slot(i)) + off,
@@ -405,7 +406,7 @@ void build_graph(GraphBuild &b, cudaStream_t cs) {
     if (ok) ok = cudaGraphAddChildGraphNode(&cn, g, b.h2d.data(), b.h2d.size(), child) == cudaSuccess;
     for (int i = 0; ok && i < in->k; ++i)
         for (int j = 0; ok && j < c; ++j) {
-            const size_t off = (size_t)j * kCopyPiece, len = std::min(kCopyPiece, bytes - off);
+            const size_t off = (size_t)j * piece, len = std::min(piece, bytes - off);
             cudaGraphNode_t *prev = j > 0 ? &b.d2h[(size_t)i * c + j - 1] : &cn;
             ok = cudaGraphAddMemcpyNode1D(&b.d2h[(size_t)i * c + j], g, prev, 1,
                                           static_cast<char *>(b.hout[i]) + off,
@@ -473,11 +474,11 @@ void launch(fftu_server_st *S, Instance *in) {
     if (locked) {
         if (in->gexec) {
             bool ok = true;
-            const size_t kCopyPiece = piece_bytes(in, bytes);
+            const size_t piece = piece_bytes(in, bytes);
             const int c = pieces(in, bytes);
             for (int i = 0; ok && i < in->k; ++i)
                 for (int j = 0; ok && j < c; ++j) {
-                    const size_t off = (size_t)j * kCopyPiece, len = std::min(kCopyPiece, bytes - off);
+                    const size_t off = (size_t)j * piece, len = std::min(piece, bytes - off);
                     const size_t q = (size_t)i * c + j;
                     ok = cudaGraphExecMemcpyNodeSetParams1D(in->gexec, in->h2d[q],
                                                            static_cast<char *>(in->in_slot(i)) + off,
@@ -669,7 +670,7 @@ void builder_main(fftu_server_st *S) {
             std::unique_lock<std::mutex> lk(S->b_mu);
             S->b_cv.wait(lk, [&] { return S->b_stop || !S->b_jobs.empty(); });
             if (S->b_jobs.empty()) return;  // stopping
-            job = static_cast<GraphBuild *>(S->b_jobs.front());
+            job = S->b_jobs.front();
             S->b_jobs.pop_front();
         }
         build_graph(*job, S->b_stream);
@@ -680,13 +681,12 @@ void builder_main(fftu_server_st *S) {
 
 // Attach graphs the builder has finished to their (idle or busy) instances.
 void collect_graphs(fftu_server_st *S) {
-    std::vector<void *> done;
+    std::vector<GraphBuild *> done;
     {
         std::lock_guard<std::mutex> lk(S->b_mu);
         done.swap(S->b_done);
     }
-    for (void *p : done) {
-        auto *b = static_cast<GraphBuild *>(p);
+    for (GraphBuild *b : done) {
         Instance *in = b->in;
         in->building = false;
         if (b->ok) {
@@ -746,13 +746,12 @@ void server_main(fftu_server_st *S) {
     if (S->builder.joinable()) S->builder.join();
     {  // graphs that finished after the last collection, and jobs never started
         std::lock_guard<std::mutex> lk(S->b_mu);
-        for (void *p : S->b_done) {
-            auto *b = static_cast<GraphBuild *>(p);
+        for (GraphBuild *b : S->b_done) {
             if (b->gexec) cudaGraphExecDestroy(b->gexec);
             if (b->graph) cudaGraphDestroy(b->graph);
             delete b;
         }
-        for (void *p : S->b_jobs) delete static_cast<GraphBuild *>(p);
+        for (GraphBuild *b : S->b_jobs) delete b;
         S->b_done.clear();
         S->b_jobs.clear();
     }
