@@ -324,9 +324,8 @@ fftu_status build_schedule(Plan &pl, int sched) {
     // Phase B: one fused pass when every p_l <= 16, else one pass per axis.
     Step s;
     const int is_double = pl.dtype == FFTU_C128;
-    const int mt3 = pl.d == 3 && pl.p[0] == pl.p[1] && pl.p[1] == pl.p[2] && pl.p[0] > 1
-                        ? phase_b3_tile_mt((int)pl.p[0], is_double)
-                        : 0;
+    const int mt3 = pl.d == 3 && pl.p[0] > 1 ? phase_b3_tile_mt((int)pl.p[0], (int)pl.p[1], (int)pl.p[2], is_double)
+                                             : 0;
     if (sched != FFTU_SCHED_GENERIC && mt3 > 0 && (pl.n[2] / pl.p[2]) % mt3 == 0 &&
         make_phase_b_fused(pl, scale, s.pb)) {
         s.kind = STEP_PHASE_B3;

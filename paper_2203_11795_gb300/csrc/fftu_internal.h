@@ -132,7 +132,7 @@ cudaError_t prepare_phase_b_fused(int is_double, int dir);
 cudaError_t prepare_phase_b3(int is_double, int dir);
 // Phase B for d = 3 with p_0 = p_1 = p_2 = P in {2, 4, 8, 16}: tile length MT
 // along the last axis (0 = not instantiated for this P and type).
-int phase_b3_tile_mt(int P, int is_double);
+int phase_b3_tile_mt(int p0, int p1, int p2, int is_double);  // 0: no 3D phase-B kernel for this grid
 cudaError_t launch_phase_b3(const PhaseBFused &b, int is_double, int dir, cudaStream_t st);
 cudaError_t launch_twiddle_table(void *dst, int64_t n, int is_double, cudaStream_t st);
 // out[i] *= mul[i] for i in [n] (used when phase B cannot fuse the multiply).

@@ -106,7 +106,7 @@ extern "C" fftu_status fftu_exec_noalloc(int d, const int64_t *n, const int64_t 
     const int units = (int)(p[0] * p[1]);
     if (units > kStaticMaxUnits || units <= kStaticRing)
         return fail(FFTU_ERR_UNSUPPORTED, "fftu_exec_noalloc: p_0 p_1 must be in (2, 4096]");
-    const int mt3 = phase_b3_tile_mt((int)p[0], 0);
+    const int mt3 = phase_b3_tile_mt((int)p[0], (int)p[1], (int)p[2], 0);
     if (mt3 == 0 || (n[2] / p[2]) % mt3 != 0)
         return fail(FFTU_ERR_UNSUPPORTED, "fftu_exec_noalloc: no fused phase-B kernel for this p");
 

@@ -774,10 +774,13 @@ cudaError_t prepare_k(int n0, int n1, int *grids) {
 //   1024^3, p = 16^3: L = 64, rows 64 = 8 x 8, axis 1 = 8 x 8, axis 0 = 8 x 8, W = 16; 64 KB tiles,
 //                   512 consumer threads, 1 CTA/SM; residue units of 32 MiB, so the ring (3 units)
 //                   is meant to stay in L2
+//   1024^3, p = 16 x 16 x 8: rows 128 = 8 x 16, axis 1 = 8 x 8, axis 0 = 8 x 8, W = 16; 32 MiB
+//                   residue units as for p = 16^3, with the 16 x 16 x 8 phase B (runs of 8)
 using K512p8 = Cfg<512, 8, 8, 8, 8, 64, 8, 8, 2, 2, true, false>;
 using K512p4 = Cfg<512, 4, 8, 8, 16, 128, 8, 4, 1, 2, true>;
 using K1024p8 = Cfg<1024, 8, 8, 8, 16, 128, 8, 4, 1, 2, true, true, 512>;
 using K1024p16 = Cfg<1024, 16, 8, 8, 8, 64, 8, 16, 1, 2, true, true, 512>;
+using K1024p16x8 = Cfg<1024, 8, 8, 8, 8, 64, 8, 16, 1, 2, true, true, 512>;
 
 template <int DIR, bool PREP>
 cudaError_t dispatch(int which, const Phase3Launch *l, cudaStream_t st, int n0, int n1, int *grid, size_t *smem) {
@@ -794,6 +797,9 @@ cudaError_t dispatch(int which, const Phase3Launch *l, cudaStream_t st, int n0, 
         case 3:
             if (smem) *smem = pipe_smem_bytes<K1024p16>(n0, n1);
             return PREP ? prepare_k<K1024p16, DIR>(n0, n1, grid) : launch_k<K1024p16, DIR>(*l, st);
+        case 4:
+            if (smem) *smem = pipe_smem_bytes<K1024p16x8>(n0, n1);
+            return PREP ? prepare_k<K1024p16x8, DIR>(n0, n1, grid) : launch_k<K1024p16x8, DIR>(*l, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -830,6 +836,10 @@ int phase_a3_select(int d, const int64_t *n, const int64_t *p, int is_double, Ph
     if (matches<K1024p16>(n, p)) {
         fill<K1024p16>(*info);
         return 3;
+    }
+    if (matches<K1024p16x8>(n, p)) {
+        fill<K1024p16x8>(*info);
+        return 4;
     }
     return -1;
 }

@@ -48,6 +48,7 @@ template <typename C, int DIR, int P0, int P1, int P2, int MT>
 __global__ void __launch_bounds__(P0 * P1 * MT / 2) phase_b3_kernel(const __grid_constant__ PhaseBFused b) {
     constexpr int HALF = MT / 2;
     constexpr int NT = P0 * P1 * HALF;
+    constexpr bool SINGLE = P0 >= 16 || P1 >= 16;  // phases 2 and 3 on single elements (register budget)
     constexpr int RS = MT;  // shared row (m2 run) stride
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
@@ -82,7 +83,20 @@ __global__ void __launch_bounds__(P0 * P1 * MT / 2) phase_b3_kernel(const __grid
             }
         }
         __syncthreads();
-        // 2. F_{P1} along s1': thread (s0', k2, pair); P0*P2*HALF work items
+        // 2. F_{P1} along s1': thread (s0', k2, pair); P0*P2*HALF work items.  With a 16-point axis
+        //    the pair would need 64 registers of values: single elements, P0*P2*MT items.
+        if constexpr (SINGLE) {
+            for (int w = tid; w < P0 * P2 * MT; w += NT) {
+                const int e = w % MT, q = w / MT;
+                const int k2 = q % P2, s0 = q / P2;
+                C v[P1];
+#pragma unroll
+                for (int r = 0; r < P1; ++r) v[r] = sm[((s0 * P1 + r) * P2 + k2) * RS + e];
+                dft_small<P1, DIR>(v);
+#pragma unroll
+                for (int r = 0; r < P1; ++r) sm[((s0 * P1 + r) * P2 + k2) * RS + e] = v[r];
+            }
+        } else
         for (int w = tid; w < P0 * P2 * HALF; w += NT) {
             const int h = w % HALF, q = w / HALF;
             const int k2 = q % P2, s0 = q / P2;
@@ -103,8 +117,28 @@ __global__ void __launch_bounds__(P0 * P1 * MT / 2) phase_b3_kernel(const __grid
             }
         }
         __syncthreads();
-        // 3. F_{P0} along s0' and store: thread (k1, k2, pair); P1*P2*HALF items
+        // 3. F_{P0} along s0' and store: thread (k1, k2, pair); P1*P2*HALF items (single elements,
+        //    P1*P2*MT items, with a 16-point axis)
         const Rl scale = (Rl)b.scale;
+        if constexpr (SINGLE) {
+            const C *mul = static_cast<const C *>(b.mul);
+            for (int w = tid; w < P1 * P2 * MT; w += NT) {
+                const int e = w % MT, q = w / MT;
+                const int k2 = q % P2, k1 = q / P2;
+                C v[P0];
+#pragma unroll
+                for (int r = 0; r < P0; ++r) v[r] = sm[((r * P1 + k1) * P2 + k2) * RS + e];
+                dft_small<P0, DIR>(v);
+                C *dst = data + (base - 2 * hp + e) + k1 * L1 * st1 + k2 * L2;
+#pragma unroll
+                for (int r = 0; r < P0; ++r) {
+                    C a = v[r];
+                    if (b.scale != 1.0) a = cscale(a, scale);
+                    if (mul) a = cmul(a, mul[(dst - data) + r * L0 * st0]);
+                    __stcs(dst + r * L0 * st0, a);
+                }
+            }
+        } else
         for (int w = tid; w < P1 * P2 * HALF; w += NT) {
             const int h = w % HALF, q = w / HALF;
             const int k2 = q % P2, k1 = q / P2;
@@ -154,11 +188,21 @@ cudaError_t prepare_t() {
                                 kMaxDynSmem);
 }
 
-// Dispatch over the instantiated (P, MT) shapes; MT is fixed per P so that a
-// tile holds 1024 (P0 P1 / 2 pairs x MT) values per s2' row group.
+// Instantiated grids: p_0 = p_1 = p_2 = P (kind P), and p = 16 x 16 x 8 (kind 168, complex64),
+// each with a fixed MT.
+int b3_kind(int p0, int p1, int p2) {
+    if (p0 == p1 && p1 == p2) return p0;
+    if (p0 == 16 && p1 == 16 && p2 == 8) return 168;
+    return 0;
+}
+
 template <typename C, int DIR, bool PREP>
 cudaError_t dispatch(int P, const PhaseBFused *b, cudaStream_t st) {
     switch (P) {
+        case 168:
+            if constexpr (sizeof(C) == 8)
+                return PREP ? prepare_t<C, DIR, 16, 16, 8, 8>() : launch_t<C, DIR, 16, 16, 8, 8>(*b, st);
+            break;
         case 2: return PREP ? prepare_t<C, DIR, 2, 2, 2, 64>() : launch_t<C, DIR, 2, 2, 2, 64>(*b, st);
         case 4: return PREP ? prepare_t<C, DIR, 4, 4, 4, 32>() : launch_t<C, DIR, 4, 4, 4, 32>(*b, st);
         case 8: return PREP ? prepare_t<C, DIR, 8, 8, 8, 16>() : launch_t<C, DIR, 8, 8, 8, 16>(*b, st);
@@ -172,19 +216,21 @@ cudaError_t dispatch(int P, const PhaseBFused *b, cudaStream_t st) {
 
 }  // namespace
 
-int phase_b3_tile_mt(int P, int is_double) {
-    switch (P) {
+int phase_b3_tile_mt(int p0, int p1, int p2, int is_double) {
+    switch (b3_kind(p0, p1, p2)) {
         case 2: return 64;
         case 4: return 32;
         case 8: return 16;
         case 16: return is_double ? 0 : 4;
+        case 168: return is_double ? 0 : 8;
     }
     return 0;
 }
 
 cudaError_t prepare_phase_b3(int is_double, int dir) {
-    for (int P : {2, 4, 8, 16}) {
-        if (phase_b3_tile_mt(P, is_double) == 0) continue;
+    for (int P : {2, 4, 8, 16, 168}) {
+        const int q = P == 168 ? 16 : P;
+        if (phase_b3_tile_mt(q, q, P == 168 ? 8 : q, is_double) == 0) continue;
         cudaError_t e;
         if (is_double)
             e = dir < 0 ? dispatch<double2, -1, true>(P, nullptr, 0) : dispatch<double2, 1, true>(P, nullptr, 0);
@@ -196,7 +242,7 @@ cudaError_t prepare_phase_b3(int is_double, int dir) {
 }
 
 cudaError_t launch_phase_b3(const PhaseBFused &b, int is_double, int dir, cudaStream_t st) {
-    const int P = b.p[0];
+    const int P = b3_kind(b.p[0], b.p[1], b.p[2]);
     if (is_double) return dir < 0 ? dispatch<double2, -1, false>(P, &b, st) : dispatch<double2, 1, false>(P, &b, st);
     return dir < 0 ? dispatch<float2, -1, false>(P, &b, st) : dispatch<float2, 1, false>(P, &b, st);
 }

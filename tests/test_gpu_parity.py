@@ -212,7 +212,7 @@ def test_full_size_2d_16384(fftu, p):
     assert emax <= tolerance(np.complex64, x.size)
 
 
-@pytest.mark.parametrize("p", [(8, 8, 8), (4, 4, 4), (16, 16, 16)], ids=["p8", "p4", "p16"])
+@pytest.mark.parametrize("p", [(8, 8, 8), (4, 4, 4), (16, 16, 16), (16, 16, 8)], ids=["p8", "p4", "p16", "p16x8"])
 def test_full_size_1024_sampled(fftu, p):
     """1024^3 complex64: forward at sampled outputs (direct O(N) sums of eq. dftd), round trip
     and Parseval over the whole array."""
@@ -324,3 +324,14 @@ def test_fused_plan_after_smaller_plan_on_same_kernel(fftu):
     ref = oracle.dft_points(x.astype(np.complex128), idx)
     got = np.array([y[i].item() for i in idx])
     assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-4
+
+
+@pytest.mark.parametrize("case", [((256, 256, 1024), (16, 16, 8)), ((256, 256, 256), (16, 16, 16))],
+                         ids=lambda c: "x".join(map(str, c[1])))
+@pytest.mark.parametrize("inverse", [False, True])
+def test_phase_b_16_grids(fftu, case, inverse):
+    """Phase B on 16 x 16 x 8 and 16^3 grids (single-element exchange stages) against the full oracle."""
+    shape, p = case
+    x = complex_uniform(717, shape, dtype=np.complex64)
+    y, _ = run_gpu(fftu, x, p, inverse=inverse)
+    assert oracle.rel_l2(y, oracle.fftn(x.astype(np.complex128), inverse=inverse)) <= tolerance(np.complex64, x.size)
