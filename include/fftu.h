@@ -164,7 +164,7 @@ fftu_status fftu_plan(int d, const int64_t *n, const int64_t *p, fftu_dtype dtyp
  * the default grid (the largest power of two up to 8 with p_l^2 | n_l, per axis).  With p == NULL and opts->tune != 0 the
  * planner measures, on scratch buffers it allocates for the duration (2 N elements), one coordinate at
  * a time: every candidate grid p_l = min(q, pmax_l), q = 1, 2, 4, ... (pmax_l: the largest power of two
- * with p_l^2 | n_l); then, for the fastest grid, the schedules (AUTO, GENERIC_A, GENERIC) unless
+ * with p_l^2 | n_l), each also with the last axis at q / 2; then, for the fastest grid, the schedules (AUTO, GENERIC_A, GENERIC) unless
  * opts->schedule fixes one; then the strided passes' tile target (2048, 4096, 8192 for complex64;
  * 1024, 2048, 4096 for complex128) and radix (8, 16) when the schedule has strided passes.  The choice
  * is remembered per (shape, dtype, direction, requested schedule, GPU) in the process's wisdom table

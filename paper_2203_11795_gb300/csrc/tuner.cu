@@ -5,7 +5,8 @@
 // Every candidate is planned, run once on scratch buffers, then timed with CUDA events (best of
 // three executions, the plan's own direction).  The search takes one coordinate at a time:
 //   1. p: p_l = min(q, pmax_l) for q = 1, 2, 4, ..., where pmax_l is the largest power of two with
-//      p_l^2 | n_l (Algorithm 2.3's condition); the untuned default (q = 8) is one of them;
+//      p_l^2 | n_l (Algorithm 2.3's condition), each also with the last axis at q / 2 (e.g. 16 x 16 x 8);
+//      the untuned default (q = 8) is one of them;
 //   2. for that p, the schedule (AUTO, GENERIC_A, GENERIC), unless the caller fixed one;
 //   3. the whole-line tile target of the strided passes, unless fixed;
 //   4. their stage radix (8 or 16), unless fixed.
@@ -122,7 +123,14 @@ bool autotune(int d, const int64_t *n, fftu_dtype dtype, fftu_dir dir, const fft
     cur.tune = 0;
     std::vector<int64_t> best_p;
     float best = -1.f;
-    // 1. the grid
+    // 1. the grid: q on every axis, and q with the last (contiguous) axis at q / 2
+    auto try_grid = [&](const std::vector<int64_t> &c) {
+        const float ms = time_candidate(d, n, c.data(), dtype, dir, cur, in, out);
+        if (ms >= 0.f && (best < 0.f || ms < best)) {
+            best = ms;
+            best_p = c;
+        }
+    };
     for (int64_t q = 1;; q *= 2) {
         std::vector<int64_t> c(d);
         bool grew = false;
@@ -130,10 +138,11 @@ bool autotune(int d, const int64_t *n, fftu_dtype dtype, fftu_dir dir, const fft
             c[l] = q < pmax[l] ? q : pmax[l];
             if (q <= pmax[l]) grew = true;
         }
-        const float ms = time_candidate(d, n, c.data(), dtype, dir, cur, in, out);
-        if (ms >= 0.f && (best < 0.f || ms < best)) {
-            best = ms;
-            best_p = c;
+        try_grid(c);
+        if (d > 1 && c[d - 1] >= 2 && c[d - 1] == q) {
+            std::vector<int64_t> h = c;
+            h[d - 1] /= 2;
+            if (h != c) try_grid(h);
         }
         if (!grew) break;
     }
