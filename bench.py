@@ -69,6 +69,7 @@ def parse_args():
                     help="write a 256 MB buffer between steps (for arrays that fit in L2); the step time is "
                          "then the sum of the phases' event intervals, the flush excluded")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-copy-streams", type=int, default=1, help="streams per copy direction in the e2e run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="leave out the torch.fft (cuFFT) context timing")
@@ -352,24 +353,61 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
+        # The step through the public API with host buffers: pinned H2D of the input, forward, inverse,
+        # D2H of the result, every step.  Copies in, transforms and copies out run on three streams, two
+        # device buffer sets deep, so that step i + 1's upload and step i - 1's download overlap step i's
+        # transforms (the transforms stay on one stream: the plans' workspaces are never shared).
         out_host = torch.empty_like(x_host).pin_memory()
-        xd = torch.empty_like(x)
+        xs_d = [torch.empty_like(x) for _ in range(2)]
+        zs_d = [z, torch.empty_like(x)]
+        K = max(1, args.e2e_copy_streams)  # each direction's copy in K pieces on K streams (copy engines)
+        s_ins = [torch.cuda.Stream(dev) for _ in range(K)]
+        s_outs = [torch.cuda.Stream(dev) for _ in range(K)]
+        s_out = s_outs[0]
+        flat_host_in, flat_host_out = x_host.view(-1), out_host.view(-1)
+        bounds = [N * k // K for k in range(K + 1)]
+        steps_e = 2 + args.e2e_steps
+        ev_in = [[torch.cuda.Event() for _ in range(K)] for _ in range(steps_e)]
+        ev_tf = [torch.cuda.Event() for _ in range(steps_e)]
+        ev_out = [[torch.cuda.Event() for _ in range(K)] for _ in range(steps_e)]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            for i in range(2 + args.e2e_steps):
-                if i == 2:
-                    torch.cuda.synchronize(dev)
-                    e0.record(stream)
-                xd.copy_(x_host, non_blocking=True)
-                fftu.fftu_exec(fwd.handle, xd.data_ptr(), y.data_ptr(), sh)
-                fftu.fftu_exec(inv.handle, y.data_ptr(), z.data_ptr(), sh)
-                out_host.copy_(z, non_blocking=True)
-            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        for i in range(steps_e):
+            b = i % 2
+            if i == 2:
+                torch.cuda.synchronize(dev)
+                e0.record(s_ins[0])
+                for k in range(1, K):
+                    s_ins[k].wait_event(e0)
+            xf, zf = xs_d[b].view(-1), zs_d[b].view(-1)
+            for k in range(K):
+                if i >= 2:
+                    s_ins[k].wait_event(ev_tf[i - 2])  # buffer b's previous input has been transformed
+                with torch.cuda.stream(s_ins[k]):
+                    xf[bounds[k]:bounds[k + 1]].copy_(flat_host_in[bounds[k]:bounds[k + 1]], non_blocking=True)
+                ev_in[i][k].record(s_ins[k])
+                stream.wait_event(ev_in[i][k])
+            if i >= 2:
+                for k in range(K):
+                    stream.wait_event(ev_out[i - 2][k])  # buffer b's previous result has been downloaded
+            fftu.fftu_exec(fwd.handle, xs_d[b].data_ptr(), y.data_ptr(), sh)
+            fftu.fftu_exec(inv.handle, y.data_ptr(), zs_d[b].data_ptr(), sh)
+            ev_tf[i].record(stream)
+            for k in range(K):
+                s_outs[k].wait_event(ev_tf[i])
+                with torch.cuda.stream(s_outs[k]):
+                    flat_host_out[bounds[k]:bounds[k + 1]].copy_(zf[bounds[k]:bounds[k + 1]], non_blocking=True)
+                ev_out[i][k].record(s_outs[k])
+        for k in range(1, K):
+            s_out.wait_event(ev_out[steps_e - 1][k])
+        e1.record(s_out)
         torch.cuda.synchronize(dev)
         e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.e2e_steps, dev)
         e2e = {"value": whole_job_value(2 * alg_bytes(shape, esize), e2e_ms, world), "unit": "GB/s",
                "h2d_bytes_per_step": N * esize, "d2h_bytes_per_step": N * esize, "ms_per_step": e2e_ms,
-               "includes": "pinned H2D of the input, forward, inverse, D2H of the result"}
+               "includes": "pinned H2D of the input, forward, inverse, D2H of the result, every step; copies "
+                           "and transforms of neighbouring steps overlap (two buffer sets; each copy direction "
+                           f"in {K} pieces on {K} streams)"}
 
     if rank == 0:
         ms_per_step = total_ms / args.steps
