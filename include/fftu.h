@@ -46,9 +46,9 @@ typedef struct fftu_plan_st *fftu_handle;
 /* Element type: interleaved complex float (c64) or complex double (c128). */
 typedef enum { FFTU_C64 = 1, FFTU_C128 = 2 } fftu_dtype;
 
-/* Sign of the exponent.  FFTU_INVERSE conjugates every weight and scales the
- * result by 1/N (Sec. 1.3: the same program with conjugated weights and the
- * outcome scaled by 1/N). */
+/* Sign of the exponent.  FFTU_INVERSE runs the forward computation with every
+ * root of unity replaced by its complex conjugate and divides the result by N
+ * (the inverse DFT as Sec. 1.3 obtains it). */
 typedef enum { FFTU_FORWARD = -1, FFTU_INVERSE = 1 } fftu_dir;
 
 typedef enum {
@@ -111,8 +111,9 @@ typedef struct {
     int precision;       /* fftu_precision */
     int layout;          /* fftu_layout */
     int workspace_mode;  /* fftu_workspace_mode */
-    int tile;            /* strided passes: elements per whole-line tile, a power of two in [1024, 8192]
-                            (complex128: [1024, 4096]); 0 = default (4096 / 2048) */
+    int tile;            /* strided passes: target elements per tile (whole lines, or the classes of a
+                            long line that fit), a power of two in [1024, 8192] (complex128: [1024, 4096]);
+                            0 = default (4096 / 2048) */
     int radix;           /* strided passes' stages: 8 = radix 8 after one smaller first stage (default,
                             also 0); 16 = radix-16 stages then one stage of the remaining factor */
     int reserved[1];     /* must be zero */
@@ -131,7 +132,7 @@ typedef struct {
     int64_t alg_bytes;         /* algorithmic HBM bytes per transform: 4 * N * sizeof(element) */
     int64_t table_bytes;       /* device bytes of twiddle tables owned by the plan */
     int64_t workspace_bytes;   /* device bytes of workspace owned by the plan */
-    int tuned;                 /* 1 when p was chosen by measurement (fftu_options.tune) */
+    int tuned;                 /* 1 when p (and the options left open) came from tuning or wisdom */
     int precision;             /* fftu_precision of the radix-16 stages */
     int64_t workspace_need;    /* device bytes of workspace the plan uses (owned or supplied) */
     int layout;                /* fftu_layout */
@@ -145,37 +146,41 @@ typedef struct {
  *   d        number of dimensions, 1 <= d <= FFTU_MAX_DIMS.
  *   n[d]     array sizes, n[0] slowest; each n_l >= 1.  This GPU build
  *            accepts powers of two only (else FFTU_ERR_UNSUPPORTED); the
- *            method needs N "sufficiently composite" (Abstract).
+ *            method itself only asks N to have many small factors (Abstract).
  *   p[d]     cyclic factors (virtual processor grid) with p_l^2 | n_l
  *            (Algorithm 2.3 input; Sec. 2.3 gives the limit p_l <= sqrt(n_l)).
- *            NULL lets the planner choose.
+ *            NULL lets the planner choose (see fftu_plan_ex).
  *   dtype    FFTU_C64 or FFTU_C128.
  *   dir      FFTU_FORWARD or FFTU_INVERSE.
  *   out      receives the handle; set to NULL on error.
  * Allocates the plan's device tables (sum_l n_l entries of w_{n_l}^e,
  * generated in FP64 on the device; cf. eq. weights) and any workspace, on the
- * current device, and synchronises once.  Not stream-ordered.
+ * current device; the tables are generated on a private stream that the call
+ * waits for (work in flight on other streams is not waited for).  Not
+ * stream-ordered.
  */
 fftu_status fftu_plan(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,
                       fftu_handle *out);
 
-/* fftu_plan with options (opts may be NULL = defaults).  With p == NULL the plan takes the process's
- * wisdom for the problem when there is some (from an earlier tuned plan or fftu_wisdom_import), else
- * the default grid (the largest power of two up to 8 with p_l^2 | n_l, per axis).  With p == NULL and opts->tune != 0 the
- * planner measures, on scratch buffers it allocates for the duration (2 N elements), one coordinate at
- * a time: every candidate grid p_l = min(q, pmax_l), q = 1, 2, 4, ... (pmax_l: the largest power of two
- * with p_l^2 | n_l), each also with the last axis at q / 2; then, for the fastest grid, the schedules (AUTO, GENERIC_A, GENERIC) unless
- * opts->schedule fixes one; then the strided passes' tile target (2048, 4096, 8192 for complex64;
- * 1024, 2048, 4096 for complex128) and radix (8, 16) when the schedule has strided passes.  The choice
- * is remembered per (shape, dtype, direction, requested schedule, GPU) in the process's wisdom table
- * (fftu_wisdom_*).  If the scratch cannot be allocated, the defaults are used. */
+/* fftu_plan with options (opts may be NULL = defaults).
+ * With p == NULL the plan takes the process's wisdom for the problem when there is some (from an
+ * earlier tuned plan or fftu_wisdom_import), else the default grid (per axis, the largest power of two
+ * up to 8 with p_l^2 | n_l).
+ * With p == NULL and opts->tune != 0 the planner measures, on scratch buffers it allocates for the
+ * duration (2 N elements), one coordinate at a time: every candidate grid p_l = min(q, pmax_l),
+ * q = 1, 2, 4, ... (pmax_l: the largest power of two with p_l^2 | n_l), each also with the last axis at
+ * q / 2; then, for the fastest grid, the schedules (AUTO, GENERIC_A, GENERIC) unless opts->schedule
+ * fixes one; then the strided passes' tile target (2048, 4096, 8192 for complex64; 1024, 2048, 4096 for
+ * complex128) and radix (8, 16), unless fixed.  The choice is remembered per (shape, dtype, direction,
+ * requested schedule, precision, GPU) in the process's wisdom table (fftu_wisdom_*).  If the scratch
+ * cannot be allocated, the defaults are used. */
 fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,
                          const fftu_options *opts, fftu_handle *out);
 
 /*
  * fftu_exec -- run the whole transform (Algorithm 2.3) on `stream`.
  *   in   device array of N elements (read only when in != out).
- *   out  device array of N elements, receives V = DFT(X) in natural order.
+ *   out  device array of N elements, receives V = DFT(X) in the plan's layout (NATURAL: row-major).
  *   in == out is allowed (in-place transform).  Other partial overlaps are
  *   not allowed.  A plan may run on one stream at a time.
  */
