@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--shape", default="512,512,512")
     ap.add_argument("--p", default="8,8,8", help="cyclic grid, or 'tune' to let the plan-time tuner choose")
     ap.add_argument("--serve", action="store_true", help="print only the serving run's line")
+    ap.add_argument("--pointwise", action="store_true",
+                    help="time forward -> pointwise product -> inverse (fftu_exec_pointwise) instead")
     ap.add_argument("--no-serve", action="store_true", help="leave the serving run out of the default line")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=0.0,
@@ -681,6 +683,94 @@ def run_serve_only(args):
         sys.exit(1)
 
 
+def run_pointwise(args):
+    """Forward transform, elementwise product in the frequency domain, inverse transform
+    (fftu_exec_pointwise), with no reordering between them; one step = one such convolution."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2203_11795_gb300 import _build
+    _build.build()
+    import paper_2203_11795_gb300 as fftu
+    from fftu_inputs import complex_uniform
+
+    shape = shape_of(args.shape)
+    p = shape_of(args.p)
+    N = math.prod(shape)
+    x = torch.from_numpy(complex_uniform(args.seed + rank, shape, dtype=np.complex64)).to(dev)
+    mul = torch.from_numpy(complex_uniform(args.seed + 5000 + rank, shape, dtype=np.complex64)).to(dev)
+    tmp, out = torch.empty_like(x), torch.empty_like(x)
+    fwd = fftu.Plan(shape, p)
+    inv = fftu.Plan(shape, p, inverse=True)
+    stream = torch.cuda.Stream(dev)
+    sh = stream.cuda_stream
+
+    def step():
+        fftu.fftu_exec_pointwise(fwd.handle, inv.handle, x.data_ptr(), mul.data_ptr(), tmp.data_ptr(),
+                                 out.data_ptr(), sh)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    if sampler:
+        sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop() if sampler else None
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
+    # the same convolution through two plain transforms and a separate product (torch only for the product)
+    ref = torch.empty_like(x)
+    with torch.cuda.stream(stream):
+        fftu.fftu_exec(fwd.handle, x.data_ptr(), tmp.data_ptr(), sh)
+        prod = tmp * mul
+        fftu.fftu_exec(inv.handle, prod.data_ptr(), ref.data_ptr(), sh)
+    torch.cuda.synchronize(dev)
+    err = float((torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref)).item())
+    fwd.check_device_status()
+    inv.check_device_status()
+    if rank == 0:
+        step_bytes = 2 * alg_bytes(shape, 8) + N * 8  # two transforms and one read of the multiplier
+        value = whole_job_value(step_bytes, ms, world)
+        peak, peak_kind = measured_peak()
+        line = {
+            "metric": "forward -> pointwise product -> inverse, algorithmic GB/s", "value": value, "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{'x'.join(map(str, shape))} complex64 convolution step "
+                                   f"(fftu_exec_pointwise), cyclic p={'x'.join(map(str, p))}",
+                       "bytes_per_step": step_bytes, "separate_product_vs_fused_rel_l2": err,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": value / world, "peak": peak, "unit": "GB/s",
+                         "frac": value / world / peak, "traffic": None, "kernel": "whole step",
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "gpu_launches": args.steps * 2 * (fwd.info["launches_phase_a"] + fwd.info["launches_phase_b"]),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+        if not err < 1e-5:
+            print(f"fused and separate convolutions differ ({err:.3g})", file=sys.stderr)
+            sys.exit(1)
+    fwd.close()
+    inv.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def uneven_shapes(count, seed, cubes=False):
     """Each n_l drawn independently from {32, 64, 128}: sizes 32^3 to 128^3, cubes included.
     cubes=True: the other reading, cubes n^3 with n drawn from {32, 64, 128}."""
@@ -837,6 +927,8 @@ def main():
         run_serve_only(args)
     elif args.batch > 0:
         run_batch(args)
+    elif args.pointwise:
+        run_pointwise(args)
     else:
         run_ours(args)
 
