@@ -246,6 +246,7 @@ def test_full_size_1024_sampled(fftu, p):
 
 @pytest.mark.parametrize("case", [((64, 64, 64), (4, 4, 4), np.complex64),      # product fused in phase B
                                   ((512, 512, 512), (8, 8, 8), np.complex64),   # ring phase A + fused product
+                                  ((256, 256, 256), (16, 16, 8), np.complex64),  # product in the 16x16x8 phase B
                                   ((32, 16, 8), (2, 2, 2), np.complex128),      # separate product pass
                                   ((256, 128), (4, 8), np.complex64)], ids=_id)
 @pytest.mark.parametrize("tmp_is_in", [False, True])
@@ -324,6 +325,26 @@ def test_fused_plan_after_smaller_plan_on_same_kernel(fftu):
     ref = oracle.dft_points(x.astype(np.complex128), idx)
     got = np.array([y[i].item() for i in idx])
     assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-4
+
+
+@pytest.mark.parametrize("case", [((256, 128, 512), (4, 2, 8), 1), ((256, 256, 512), (2, 2, 4), 2)],
+                         ids=["512rows_p4x2x8_ring", "512rows_p2x2x4_two_kernels"])
+def test_fused_phase_a_matches_model(fftu, case):
+    """The fused phase A alone (sub-FFTs and twiddle of Superstep 0, Put of Superstep 1) against the
+    CPU model, n_0 != n_1 included, both directions, as the persistent ring kernel and as the
+    two-kernel schedule (16 and 64 MiB residue units); then phase B alone on the model's W."""
+    shape, p, launches = case
+    x = complex_uniform(4244, shape, dtype=np.complex64)
+    for inverse in (False, True):
+        wa, info = run_gpu(fftu, x, p, inverse=inverse, phase=fftu.FFTU_PHASE_A)
+        assert info["launches_phase_a"] == launches
+        w_ref = cm.phase_a(x.astype(np.complex128), p, inverse=inverse)
+        assert oracle.rel_l2(wa, w_ref) <= tolerance(np.complex64, x.size)
+        assert oracle.max_abs_rel(wa, w_ref) <= tolerance(np.complex64, x.size)
+        w_in = w_ref.astype(np.complex64)
+        vb, _ = run_gpu(fftu, w_in, p, inverse=inverse, phase=fftu.FFTU_PHASE_B)
+        assert oracle.rel_l2(vb, cm.phase_b(w_in.astype(np.complex128), p, inverse=inverse)) <= \
+            tolerance(np.complex64, x.size)
 
 
 @pytest.mark.parametrize("case", [((256, 256, 1024), (16, 16, 8)), ((256, 256, 256), (16, 16, 16))],
