@@ -122,6 +122,23 @@ def oracle_cpu_run(shape, seed, reps=1):
     return (time.perf_counter() - t0) / reps, cores
 
 
+def torch_cpu_fft_run(shape, seed, reps=3):
+    """torch.fft on the host (complex64, torch's own threads): context for the oracle's numbers."""
+    import numpy as np
+    import torch
+    from fftu_inputs import complex_uniform
+    x = torch.from_numpy(complex_uniform(seed, shape, dtype=np.complex64))
+    torch.fft.ifftn(torch.fft.fftn(x))  # warm-up (plans, allocations)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        torch.fft.ifftn(torch.fft.fftn(x))
+    dt = (time.perf_counter() - t0) / reps
+    return {"impl": "torch.fft.fftn + ifftn on the host (complex64)", "threads": torch.get_num_threads(),
+            "shape": "x".join(map(str, shape)), "reps": reps, "seconds_per_rep": dt,
+            "value": 2 * alg_bytes(shape, 8) / dt / 1e9, "unit": "GB/s",
+            "note": "context, not a baseline: an optimized CPU FFT library, not the oracle"}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -465,6 +482,24 @@ def run_ours(args):
             cpu["single_thread"] = {"value": 2 * alg_bytes(one, esize) / t1 / 1e9, "unit": "GB/s", "cores": 1,
                                     "seconds_per_rep": t1,
                                     "sample": "same oracle, 1 thread, forward+inverse of one 128^3 array, 3 reps"}
+            small = (64, 64, 64)
+            oracle.set_threads(1)
+            try:
+                ts1, _ = oracle_cpu_run(small, args.seed, reps=3)
+            finally:
+                oracle.set_threads(0)
+            tsa, _ = oracle_cpu_run(small, args.seed, reps=3)
+            cpu["sizes"] = [{"shape": "x".join(map(str, sh)), "cores": c, "reps": r, "seconds_per_rep": t,
+                             "value": 2 * alg_bytes(sh, esize) / t / 1e9, "unit": "GB/s"}
+                            for sh, c, r, t in ((small, 1, 3, ts1), (small, cores, 3, tsa), (one, 1, 3, t1),
+                                                (sample, cores, args.cpu_reps, t_cpu))]
+            cpu["skipped"] = ("1024^3: one forward+inverse pair of the oracle takes about 8x the 512^3 time and "
+                              "16 GiB per FP64 array; left out to keep the CPU sample bounded")
+            if esize == 8:
+                try:
+                    cpu["torch_cpu_context"] = torch_cpu_fft_run(sample, args.seed)
+                except Exception as exc:  # context only; reported, never silently dropped
+                    cpu["torch_cpu_context"] = {"error": repr(exc)}
         line = {
             "metric": METRIC, "metric_detail": METRIC_DETAIL,
             "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
