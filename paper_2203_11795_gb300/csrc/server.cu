@@ -840,11 +840,18 @@ fftu_status fftu_server_submit(fftu_server S, const fftu_request *req) {
         fftu::record_error("server: bad d, dtype or direction");
         return FFTU_ERR_ARG;
     }
-    for (int l = 0; l < req->d; ++l)
+    int64_t N = 1;
+    for (int l = 0; l < req->d; ++l) {
         if (req->n[l] < 1 || (req->n[l] & (req->n[l] - 1))) {
             fftu::record_error("server: every n_l must be a power of two");
             return req->n[l] < 1 ? FFTU_ERR_ARG : FFTU_ERR_UNSUPPORTED;
         }
+        if (req->n[l] > ((int64_t)1 << 40) || N > ((int64_t)1 << 40) / req->n[l]) {  // the plans' limit
+            fftu::record_error("server: N exceeds 2^40 elements");
+            return FFTU_ERR_ARG;
+        }
+        N *= req->n[l];
+    }
     Req q;
     q.r = *req;
     q.t_submit = S->now();
