@@ -568,8 +568,8 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
                 set_err("p[%d] = %lld < 1", l, (long long)p[l]);
                 return FFTU_ERR_ARG;
             }
-            if (p[l] > n[l]) {  // then p_l^2 cannot divide n_l (and squaring p_l could overflow)
-                set_err("p[%d] = %lld exceeds n[%d] = %lld", l, (long long)p[l], l, (long long)n[l]);
+            if (p[l] > n[l] / p[l]) {  // p_l^2 > n_l: it cannot divide (and squaring p_l could overflow)
+                set_err("p[%d]^2 exceeds n[%d] = %lld (p[%d] = %lld)", l, l, (long long)n[l], l, (long long)p[l]);
                 return FFTU_ERR_DIVISIBILITY;
             }
             if (n[l] % (p[l] * p[l]) != 0) {

@@ -90,7 +90,7 @@ extern "C" fftu_status fftu_exec_noalloc(int d, const int64_t *n, const int64_t 
         return fail(FFTU_ERR_ARG, "fftu_exec_noalloc: in/out must be 16-byte aligned");
     for (int l = 0; l < 3; ++l) {
         if (n[l] < 1 || p[l] < 1) return fail(FFTU_ERR_ARG, "fftu_exec_noalloc: n_l and p_l must be >= 1");
-        if (p[l] > n[l] || n[l] % (p[l] * p[l]) != 0)
+        if (p[l] > n[l] / p[l] || n[l] % (p[l] * p[l]) != 0)
             return fail(FFTU_ERR_DIVISIBILITY, "fftu_exec_noalloc: p_l^2 must divide n_l");
         if (n[l] > kStaticMaxN)
             return fail(FFTU_ERR_UNSUPPORTED, "fftu_exec_noalloc: n_l above 4096 (static twiddle table size)");

@@ -83,6 +83,55 @@ float time_candidate(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype
     return ok ? best : -1.f;
 }
 
+// An imported line is kept only if its key and choices describe a plan fftu_plan_ex would accept:
+// key d:n_0,...,n_{d-1}:dtype:dir:schedule:precision:gpu with power-of-two n_l, and a grid with
+// p_l^2 | n_l, a known schedule, a tile of 0 or a power of two in [1024, 8192] (4096 for complex128)
+// and a radix of 0, 8 or 16.  A file is input from outside the process: a bad line must not reach a
+// plan.
+bool valid_entry(const std::string &key, const Wise &w) {
+    const std::vector<std::string> f = [&] {
+        std::vector<std::string> parts;
+        size_t start = 0;
+        for (size_t i = 0; i <= key.size(); ++i)
+            if (i == key.size() || key[i] == ':') {
+                parts.push_back(key.substr(start, i - start));
+                start = i + 1;
+            }
+        return parts;
+    }();
+    if (f.size() < 7) return false;  // fields 6.. are the GPU name
+    char *end = nullptr;
+    const long d = std::strtol(f[0].c_str(), &end, 10);
+    if (*end || d < 1 || d > FFTU_MAX_DIMS || (long)w.p.size() != d) return false;
+    std::vector<long long> n;
+    for (size_t start = 0; start <= f[1].size();) {
+        size_t stop = f[1].find(',', start);
+        if (stop == std::string::npos) stop = f[1].size();
+        const std::string tok = f[1].substr(start, stop - start);
+        const long long v = std::strtoll(tok.c_str(), &end, 10);
+        if (tok.empty() || *end || v < 1 || v > (1ll << 40) || (v & (v - 1))) return false;
+        n.push_back(v);
+        start = stop + 1;
+    }
+    if ((long)n.size() != d) return false;
+    const long dtype = std::strtol(f[2].c_str(), &end, 10);
+    if (*end || (dtype != FFTU_C64 && dtype != FFTU_C128)) return false;
+    const long dir = std::strtol(f[3].c_str(), &end, 10);
+    if (*end || (dir != FFTU_FORWARD && dir != FFTU_INVERSE)) return false;
+    const long sched = std::strtol(f[4].c_str(), &end, 10);
+    if (*end || sched < FFTU_SCHED_AUTO || sched > FFTU_SCHED_GENERIC_A) return false;
+    const long prec = std::strtol(f[5].c_str(), &end, 10);
+    if (*end || prec < FFTU_PREC_NATIVE || prec > FFTU_PREC_SPLIT_FP16) return false;
+    for (long l = 0; l < d; ++l) {
+        const long long q = w.p[l];
+        if (q < 1 || q > n[l] / q || (q & (q - 1)) || n[l] % (q * q) != 0) return false;
+    }
+    if (w.schedule < FFTU_SCHED_AUTO || w.schedule > FFTU_SCHED_GENERIC_A) return false;
+    const int tmax = dtype == FFTU_C128 ? 4096 : 8192;
+    if (w.tile != 0 && (w.tile < 1024 || w.tile > tmax || (w.tile & (w.tile - 1)))) return false;
+    return w.radix == 0 || w.radix == 8 || w.radix == 16;
+}
+
 }  // namespace
 
 // The wisdom entry for the problem, if any (no measurement).
@@ -240,6 +289,7 @@ fftu_status fftu_wisdom_import(const char *path) {
         w.schedule = sched;
         w.tile = tile;
         w.radix = radix;
+        if (!fftu::valid_entry(k, w)) continue;  // never let a malformed line reach a plan
         fftu::g_wisdom[k] = w;
     }
     std::fclose(f);

@@ -56,6 +56,7 @@ def test_status_strings_and_version():
     ([64, 0], [1, 1], 1),            # n_l < 1
     ([64, 64], [0, 1], 1),           # p_l < 1
     ([64, 64], [1 << 32, 1], 2),     # p_l > n_l (p_l^2 would overflow 64 bits)
+    ([1 << 40], [1 << 39], 2),       # p_l <= n_l but p_l^2 > n_l (and overflows 64 bits)
 ])
 def test_plan_validation(n, p, code):
     import paper_2203_11795_gb300 as f
