@@ -275,8 +275,12 @@ fftu_status fftu_batch_check_status(fftu_batch batch);
 fftu_status fftu_batch_destroy(fftu_batch batch);
 
 /* Wisdom: the tuned choices as text lines "fftu-wisdom-v2 <key> <p_1,...,p_d> <schedule> <tile> <radix>"
- * (lines "fftu-wisdom-v1 <key> <p_1,...,p_d>" are read as grids with the other choices left to the
- * defaults).  Export writes the process's table, import merges a file into it, forget clears it. */
+ * with key "d:n_1,...,n_d:dtype:dir:schedule:precision:gpu_name" (lines "fftu-wisdom-v1 <key>
+ * <p_1,...,p_d>", whose key has no precision field, are read as grids with the other choices left to
+ * the defaults).  Export writes the process's table, import merges a file into it, forget clears it.
+ * Import skips every line that no plan would accept (a grid with p_l^2 not dividing n_l, a shape that
+ * is not a power of two, an unknown schedule, tile or radix, a malformed key) and lines of other
+ * tools; FFTU_ERR_ARG only when the file cannot be opened. */
 fftu_status fftu_wisdom_export(const char *path);
 fftu_status fftu_wisdom_import(const char *path);
 fftu_status fftu_wisdom_forget(void);
