@@ -123,3 +123,50 @@ def test_planted_model_mistakes_fail(monkeypatch):
 
     monkeypatch.setattr(cm, "superstep1", bad_put)
     assert oracle.rel_l2(cm.run(x, p), ref) > 1e-3
+
+
+# Sec. 2.3 prints the largest processor counts the single-exchange method allows, p_max = prod_l p_l
+# with p_l the largest power of two whose square divides n_l: 32^3 = 32,768 for 1024^3, 16^3 = 4096
+# for 256^3 and 512^3, and 32,768 for the 2^24 x 64 array.
+PRINTED_PMAX = [((1024, 1024, 1024), 32768), ((512, 512, 512), 4096), ((256, 256, 256), 4096),
+                ((1 << 24, 64), 32768)]
+
+
+def _largest_grid(shape):
+    grid = []
+    for n_l in shape:
+        q = 1
+        while n_l % ((2 * q) * (2 * q)) == 0:
+            q *= 2
+        grid.append(q)
+    return tuple(grid)
+
+
+@pytest.mark.parametrize("shape,pmax", PRINTED_PMAX, ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else str(v))
+def test_printed_pmax(shape, pmax):
+    """The model's condition p_l^2 | n_l admits exactly the grids of the printed p_max: the largest grid
+    is accepted, doubling any axis of it is refused, and its product is the printed number."""
+    grid = _largest_grid(shape)
+    assert int(np.prod(grid)) == pmax
+    cm._check(shape, grid)
+    for l in range(len(shape)):
+        bigger = list(grid)
+        bigger[l] *= 2
+        with pytest.raises(ValueError):
+            cm._check(shape, tuple(bigger))
+
+
+@pytest.mark.parametrize("shape,pmax", PRINTED_PMAX, ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else str(v))
+def test_boundary_refuses_grids_beyond_printed_pmax(shape, pmax):
+    """fftu_plan refuses (FFTU_ERR_DIVISIBILITY, before touching a device) every grid that doubles
+    one axis of the largest admissible grid."""
+    from paper_2203_11795_gb300 import _build
+    _build.build()
+    import paper_2203_11795_gb300 as f
+    grid = _largest_grid(shape)
+    for l in range(len(shape)):
+        bigger = list(grid)
+        bigger[l] *= 2
+        with pytest.raises(f.FFTUError) as ei:
+            f.fftu_plan(len(shape), list(shape), bigger, f.FFTU_C64, f.FFTU_FORWARD)
+        assert ei.value.status == 2
