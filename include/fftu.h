@@ -237,20 +237,41 @@ fftu_status fftu_check_device_status(fftu_handle plan);
  * allocator).  No plan is needed; the arguments mean what they mean for
  * fftu_plan and fftu_exec, with these limits:
  *   - d = 3, FFTU_C64, p_0 = p_1 = p_2, and a shape with a fused kernel whose
- *     residue unit (n_0 n_1 n_2 / (p_0 p_1) elements) fits a 16 MiB slot
- *     (e.g. 512^3 with p = 8^3); otherwise FFTU_ERR_UNSUPPORTED;
+ *     residue unit (n_0 n_1 n_2 / (p_0 p_1) elements) fits a 16 MiB slot.
+ *     With the fused kernels this build has, that is 512^3 with p = 8^3 only;
+ *     every other problem returns FFTU_ERR_UNSUPPORTED;
  *   - in != out (FFTU_ERR_ARG otherwise); both 16-byte aligned device pointers.
- * Scratch, counters and twiddle tables live in static device arrays (about
- * 32 MiB, held by every GPU that loads this part of the library until the
- * process exits).  The first call on a device (with that device current) looks
- * up their addresses; make it before any stream capture.  All calls share the
- * arrays: calls that overlap on the GPU race and give wrong results, so order
- * them on one stream.  The counters are cleared and the tables rewritten on the
- * stream by each call as needed.  Calls no cudaMalloc, cudaFree or allocating
+ * Scratch, counters, twiddle tables and a status word live in static device
+ * arrays (about 32 MiB, held by every GPU that loads this part of the library
+ * until the process exits).  Set-up: the first call on a device (with that
+ * device current) looks up their addresses, and the first call with a given
+ * axis length writes that length's twiddle table into a slot of its own (once
+ * per device, then never rewritten) and waits for it; make those first calls
+ * before any stream capture -- made under capture they return FFTU_ERR_ARG.
+ * All calls share the arrays: calls that overlap on the GPU race and give
+ * wrong results, so order them on one stream.  The counters are cleared on the
+ * stream by each call.  A bounded device wait that expires leaves that call's
+ * output invalid and sets the shared status word; read it with
+ * fftu_noalloc_check_status.  Calls no cudaMalloc, cudaFree or allocating
  * library routine.
  */
 fftu_status fftu_exec_noalloc(int d, const int64_t *n, const int64_t *p, fftu_dtype dtype, fftu_dir dir,
                               const void *in, void *out, void *stream);
+
+/* fftu_noalloc_check_status -- read and clear the status word that fftu_exec_noalloc's kernels share
+ * on the current device.  The read is ordered after the work queued on `stream` and the call waits
+ * for it (not allowed while `stream` is capturing: FFTU_ERR_ARG).  Returns FFTU_OK if no device wait
+ * has expired since the last check, FFTU_ERR_TIMEOUT if one has (the output of the call it belonged to
+ * is invalid), FFTU_ERR_INTERNAL for any other recorded code.  No allocation.  The paper has no
+ * counterpart (failure detection of the allocation-free entry point). */
+fftu_status fftu_noalloc_check_status(void *stream);
+
+/* fftu_noalloc_selftest_timeout -- failure-detection self-test of that status word: runs the library's
+ * bounded device wait, on `stream`, on a static word nothing advances, with a budget of limit_s seconds
+ * (0.001..2), so that the wait expires and records FFTU_ERR_TIMEOUT in the word
+ * fftu_noalloc_check_status reads.  Waits for the stream.  Nothing traps; the context stays usable.
+ * Returns FFTU_ERR_ARG for a budget out of range or a capturing stream. */
+fftu_status fftu_noalloc_selftest_timeout(double limit_s, void *stream);
 
 /*
  * Batches: many transforms of different shapes in one persistent kernel launch.
@@ -303,6 +324,14 @@ fftu_status fftu_set_workspace(fftu_handle plan, void *workspace, size_t bytes);
  * it waited.  Returns FFTU_OK when that happened, FFTU_ERR_INTERNAL if the status was not set.
  * Synchronises its own stream; the context stays usable. */
 fftu_status fftu_selftest_bounded_wait(double limit_s, double *waited_s);
+
+/* Measurement helper (not part of the method): the sustained FP64 fused multiply-add rate of the
+ * current device in GFLOP/s (2 flops per FMA), from a kernel that keeps every SM's FP64 pipe busy with
+ * independent FMA chains, timed with CUDA events; best of `reps` (1..100) timed launches after one
+ * warm-up.  complex128 transforms are bound by this rate rather than by HBM bandwidth on GB300, so
+ * their roofline is stated against it.  Allocates and frees 8 bytes of device memory and a stream;
+ * synchronises that stream.  FFTU_ERR_ARG for a NULL gflops or reps out of range. */
+fftu_status fftu_measure_fp64_rate(int reps, double *gflops);
 
 /* Static string for a status code. */
 const char *fftu_status_string(fftu_status s);

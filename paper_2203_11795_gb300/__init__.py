@@ -32,9 +32,11 @@ STATUS_NAMES = {0: "FFTU_OK", 1: "FFTU_ERR_ARG", 2: "FFTU_ERR_DIVISIBILITY", 3: 
 # Every entry point the header declares (checked by the test suite).
 EXPORTS = ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_exec_pointwise", "fftu_destroy",
            "fftu_plan_info",
-           "fftu_check_device_status", "fftu_exec_noalloc", "fftu_batch_create", "fftu_batch_exec",
+           "fftu_check_device_status", "fftu_exec_noalloc", "fftu_noalloc_check_status",
+           "fftu_noalloc_selftest_timeout", "fftu_batch_create", "fftu_batch_exec",
            "fftu_batch_check_status", "fftu_batch_destroy", "fftu_wisdom_export", "fftu_wisdom_import",
            "fftu_wisdom_forget", "fftu_workspace_size", "fftu_set_workspace", "fftu_selftest_bounded_wait",
+           "fftu_measure_fp64_rate",
            "fftu_status_string",
            "fftu_last_error", "fftu_version",
            # include/fftu_serve.h
@@ -108,6 +110,8 @@ def _load_library() -> ctypes.CDLL:
     lib.fftu_plan_info.argtypes = [h, ctypes.POINTER(fftu_info)]
     lib.fftu_check_device_status.argtypes = [h]
     lib.fftu_exec_noalloc.argtypes = [ctypes.c_int, i64p, i64p, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+    lib.fftu_noalloc_check_status.argtypes = [vp]
+    lib.fftu_noalloc_selftest_timeout.argtypes = [ctypes.c_double, vp]
     lib.fftu_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(h), ctypes.POINTER(h)]
     lib.fftu_batch_exec.argtypes = [h, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     lib.fftu_batch_check_status.argtypes = [h]
@@ -118,6 +122,7 @@ def _load_library() -> ctypes.CDLL:
     lib.fftu_workspace_size.argtypes = [h, ctypes.POINTER(ctypes.c_size_t)]
     lib.fftu_set_workspace.argtypes = [h, vp, ctypes.c_size_t]
     lib.fftu_selftest_bounded_wait.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.fftu_measure_fp64_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.fftu_server_create.argtypes = [ctypes.POINTER(fftu_server_config), ctypes.POINTER(h)]
     lib.fftu_server_submit.argtypes = [h, ctypes.POINTER(fftu_request)]
     lib.fftu_server_poll.argtypes = [h, ctypes.POINTER(fftu_completion), ctypes.c_int]
@@ -129,10 +134,11 @@ def _load_library() -> ctypes.CDLL:
     lib.fftu_last_error.restype = ctypes.c_char_p
     lib.fftu_version.restype = ctypes.c_char_p
     for name in ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_exec_pointwise", "fftu_destroy",
-                 "fftu_plan_info", "fftu_check_device_status", "fftu_exec_noalloc", "fftu_batch_create",
+                 "fftu_plan_info", "fftu_check_device_status", "fftu_exec_noalloc", "fftu_noalloc_check_status",
+                 "fftu_noalloc_selftest_timeout", "fftu_batch_create",
                  "fftu_batch_exec", "fftu_batch_check_status", "fftu_batch_destroy", "fftu_wisdom_export",
                  "fftu_wisdom_import", "fftu_wisdom_forget", "fftu_workspace_size", "fftu_set_workspace",
-                 "fftu_selftest_bounded_wait",
+                 "fftu_selftest_bounded_wait", "fftu_measure_fp64_rate",
                  "fftu_server_create", "fftu_server_submit",
                  "fftu_server_poll", "fftu_server_drain", "fftu_server_stats_get", "fftu_server_destroy"):
         getattr(lib, name).restype = ctypes.c_int
@@ -226,6 +232,16 @@ def fftu_exec_noalloc(d: int, n, p, dtype: int, direction: int, in_ptr: int, out
                                   stream or None), "fftu_exec_noalloc")
 
 
+def fftu_noalloc_check_status(stream: int = 0) -> None:
+    """Read and clear fftu_exec_noalloc's shared device status word (raises FFTUError on a recorded error)."""
+    _check(_lib.fftu_noalloc_check_status(stream or None), "fftu_noalloc_check_status")
+
+
+def fftu_noalloc_selftest_timeout(limit_s: float, stream: int = 0) -> None:
+    """Let a bounded device wait expire into fftu_exec_noalloc's status word (failure-detection self-test)."""
+    _check(_lib.fftu_noalloc_selftest_timeout(float(limit_s), stream or None), "fftu_noalloc_selftest_timeout")
+
+
 def fftu_batch_create(plans) -> int:
     hs = (ctypes.c_void_p * len(plans))(*plans)
     b = ctypes.c_void_p()
@@ -308,6 +324,13 @@ def fftu_workspace_size(plan: int) -> int:
 
 def fftu_set_workspace(plan: int, ptr, nbytes: int) -> None:
     _check(_lib.fftu_set_workspace(plan, ptr, int(nbytes)), "fftu_set_workspace")
+
+
+def fftu_measure_fp64_rate(reps: int = 3) -> float:
+    """Sustained FP64 FMA rate of the current device, GFLOP/s (best of reps timed launches)."""
+    g = ctypes.c_double(0.0)
+    _check(_lib.fftu_measure_fp64_rate(int(reps), ctypes.byref(g)), "fftu_measure_fp64_rate")
+    return float(g.value)
 
 
 def fftu_selftest_bounded_wait(limit_s: float) -> float:

@@ -83,6 +83,8 @@ struct Phase3Launch {
     int grid, grid1, grid2;  // persistent ring kernel; stage-1 and stage-2 kernels
     long long spin_limit_ns;
 };
+// Number of compile-time phase-A configurations; phase_a3_select returns an index below it, or -1.
+constexpr int kPhaseA3Configs = 5;
 int phase_a3_select(int d, const int64_t *n, const int64_t *p, int is_double, Phase3Info *info);
 // grids[0..2]: stage-1, stage-2 and ring kernel grid sizes (SMs x resident CTAs).
 cudaError_t prepare_phase_a3(int which, int dir, int n0, int n1, int *grids, size_t *smem);

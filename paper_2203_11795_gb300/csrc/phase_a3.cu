@@ -782,6 +782,9 @@ using K1024p8 = Cfg<1024, 8, 8, 8, 16, 128, 8, 4, 1, 2, true, true, 512>;
 using K1024p16 = Cfg<1024, 16, 8, 8, 8, 64, 8, 16, 1, 2, true, true, 512>;
 using K1024p16x8 = Cfg<1024, 8, 8, 8, 8, 64, 8, 16, 1, 2, true, true, 512>;
 
+// dispatch() below handles exactly the configurations 0 .. kPhaseA3Configs - 1.
+static_assert(kPhaseA3Configs == 5, "phase_a3_select / dispatch and kPhaseA3Configs disagree");
+
 template <int DIR, bool PREP>
 cudaError_t dispatch(int which, const Phase3Launch *l, cudaStream_t st, int n0, int n1, int *grid, size_t *smem) {
     switch (which) {
