@@ -1,12 +1,16 @@
 """Split-precision tensor-core radix-16 stages (fftu_options.precision) against the FP64 oracle.
 
-Error model: an operand v is carried as v_hi + v_lo in a 16-bit type with unit roundoff u
-(bfloat16 2^-8, float16 2^-11), so its representation error is at most u^2 |v|; with the
-dropped lo x lo product, each real 16-point product has absolute error at most 3 u^2 |F| |x|
-entrywise, i.e. a relative L2 error of at most 12 u^2 per radix-16 stage (|F| has 16 ones per
-row against ||F||_2 = 4).  Stages compose additively to first order, so the tolerance is
-S * 12 u^2 plus the FP32 budget of the native path (1e-5 log2 N), S = radix-16 stages per
-element.  Inputs: uniform[-1, 1) and log-uniform magnitudes over [1e-3, 1e3)."""
+Assertion: every result meets the complex64 bound the native path is held to, relative L2
+<= 1e-5 log2 N against the FP64 oracle, so the split forms are reported at the same stated
+accuracy as the FP32 CUDA-core path.
+
+Error model (printed beside each result as a diagnostic, not asserted): an operand v is carried
+as v_hi + v_lo in a 16-bit type with unit roundoff u (bfloat16 2^-8, float16 2^-11), so its
+representation error is at most u^2 |v|; with the dropped lo x lo product, each real 16-point
+product has absolute error at most 3 u^2 |F| |x| entrywise, i.e. a relative L2 error of at most
+12 u^2 per radix-16 stage (|F| has 16 ones per row against ||F||_2 = 4).  Stages compose
+additively to first order, so the model's bound is S * 12 u^2 plus the FP32 budget, S =
+radix-16 stages per element.  Inputs: uniform[-1, 1) and log-uniform magnitudes over [1e-3, 1e3)."""
 import math
 
 import numpy as np
@@ -35,9 +39,14 @@ def tc_stages(shape, p):
     return sum(int(math.log2(n // q)) // 4 for n, q in zip(shape, p))
 
 
-def tolerance(shape, p, precision):
-    N = math.prod(shape)
-    return tc_stages(shape, p) * 12 * U[precision] ** 2 + 1e-5 * math.log2(N)
+def tolerance(shape):
+    """The complex64 bound every result is asserted against."""
+    return 1e-5 * math.log2(math.prod(shape))
+
+
+def model_bound(shape, p, precision):
+    """First-order error model of the split stages (diagnostic only)."""
+    return tc_stages(shape, p) * 12 * U[precision] ** 2 + tolerance(shape)
 
 
 def make(kind, seed, shape):
@@ -74,8 +83,8 @@ def test_split_precision_matches_oracle(fftu, case, precision, kind, inverse):
     assert info["precision"] == precision and info["schedule"] == fftu.FFTU_SCHED_GENERIC_A
     err = oracle.rel_l2(y, oracle.fftn(x.astype(np.complex128), inverse=inverse))
     print(f"split {'bf16' if precision == 1 else 'fp16'} {kind} {shape} {'inv' if inverse else 'fwd'}: "
-          f"rel L2 {err:.3e}")
-    assert err <= tolerance(shape, p, precision)
+          f"rel L2 {err:.3e} (bound {tolerance(shape):.1e}, error model {model_bound(shape, p, precision):.1e})")
+    assert err <= tolerance(shape)
 
 
 def test_full_size_512_errors(fftu):
@@ -89,9 +98,8 @@ def test_full_size_512_errors(fftu):
         for precision in (0, 1, 2):
             y, _ = run(fftu, x, p, precision)
             err = oracle.rel_l2(y, ref)
-            print(f"512^3 {kind} precision {precision}: rel L2 {err:.3e}")
-            tol = 1e-5 * math.log2(x.size) if precision == 0 else tolerance(shape, p, precision)
-            assert err <= tol
+            print(f"512^3 {kind} precision {precision}: rel L2 {err:.3e} (bound {tolerance(shape):.1e})")
+            assert err <= tolerance(shape)
             del y
 
 
