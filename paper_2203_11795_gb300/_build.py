@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import hashlib
 import os
 import shutil
 import subprocess
@@ -40,16 +41,32 @@ def _deps():
         glob.glob(os.path.join(HERE, "..", "include", "*.h"))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+STAMP = LIB + ".sha256"
+
+
+def source_hash(extra_flags=None) -> str:
+    """SHA-256 over every source and header the library is built from, plus the flags."""
+    h = hashlib.sha256()
+    for f in sorted(os.path.realpath(x) for x in _deps()):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    h.update(" ".join(ARCH + list(extra_flags or [])).encode())
+    return h.hexdigest()
+
+
+def up_to_date(extra_flags=None) -> bool:
+    """True when libfftu.so exists and was built from exactly the current sources (content hash, not mtime)."""
+    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(f) <= t for f in _deps())
+    with open(STAMP) as fh:
+        return fh.read().strip() == source_hash(extra_flags)
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    if not force and up_to_date():
+    if not force and up_to_date(extra_flags):
         return LIB
+    digest = source_hash(extra_flags)
     nvcc = _nvcc()
     os.makedirs(OBJ, exist_ok=True)
     common = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -78,6 +95,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if res.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{res.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP + f".tmp{os.getpid()}", "w") as fh:
+        fh.write(digest + "\n")
+    os.replace(STAMP + f".tmp{os.getpid()}", STAMP)
     return LIB
 
 
