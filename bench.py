@@ -31,7 +31,8 @@ if ROOT not in sys.path:
 
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 8000.0  # the nominal HBM3e figure the target is also quoted against
-FP64_PEAK_GFLOPS = 1250.0  # GB300 FP64 nominal: complex128 transforms are bound by FP64 arithmetic
+FP64_PEAK_GFLOPS = 1250.0  # nominal; used only if the device measurement fails
+REF_BUDGET_S = 240.0  # wall-time budget of the reference arm's steps  # GB300 FP64 nominal: complex128 transforms are bound by FP64 arithmetic
 METRIC = "3D FFT HBM GB/s & % roofline at 512^3 c64; mixed-request p50/p99 latency"
 METRIC_DETAIL = ("value: algorithmic HBM GB/s, B_alg = 4 N b bytes per transform (b = element size), "
                  "one forward + one inverse transform per step; the mixed-request p50/p99 latency is the "
@@ -65,7 +66,13 @@ def parse_args():
     ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
     ap.add_argument("--precision", choices=["native", "bf16", "fp16"], default="native",
                     help="radix-16 stages on CUDA cores (native) or as split bf16/fp16 tensor-core contractions")
-    ap.add_argument("--inputs", choices=["uniform", "loguniform"], default="uniform")
+    ap.add_argument("--inputs", choices=["uniform", "loguniform", "device", "device_loguniform"], default="uniform",
+                    help="uniform / loguniform: fftu_inputs on the host; device / device_loguniform: the same "
+                         "distributions drawn on the GPU by torch's seeded generator (large secondary runs)")
+    ap.add_argument("--tile", type=int, default=0, help="strided-pass tile target (0 = default)")
+    ap.add_argument("--radix", type=int, default=0, help="strided-pass stage radix (0 = default)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="leave the secondary configurations out of the default line")
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--flush-l2", action="store_true",
                     help="write a 256 MB buffer between steps (for arrays that fit in L2); the step time is "
@@ -77,7 +84,6 @@ def parse_args():
     ap.add_argument("--no-cufft", action="store_true", help="leave out the torch.fft (cuFFT) context timing")
     ap.add_argument("--cpu-sample", default="512,512,512", help="oracle sample shape for cpu_baseline")
     ap.add_argument("--cpu-reps", type=int, default=3, help="oracle forward+inverse repetitions for cpu_baseline")
-    ap.add_argument("--ref-sample", default="256,256,256", help="oracle sample shape per reference step")
     a = ap.parse_args()
     a.warmup = max(3, a.warmup)
     return a
@@ -106,6 +112,43 @@ def measured_peak():
 
 def alg_bytes(shape, esize):
     return 4 * math.prod(shape) * esize
+
+
+def device_inputs(shape, t_dtype, seed, dev, loguniform=False):
+    """Seeded synthetic inputs drawn on the GPU (torch's Philox generator): Re and Im i.i.d.
+    uniform[-1, 1), or (loguniform) magnitudes 10^U[-3, 3) with a uniform phase.  Used for the large
+    secondary runs, whose host-side generation would dominate the bench's wall time; the parity tests
+    use fftu_inputs' SplitMix64 arrays."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(seed))
+    real = torch.float32 if t_dtype == torch.complex64 else torch.float64
+    n = math.prod(shape)
+    u = torch.rand(2 * n, generator=g, device=dev, dtype=real)
+    if loguniform:
+        mag = torch.pow(10.0, -3.0 + 6.0 * u[0::2])
+        ph = 2.0 * math.pi * u[1::2]
+        x = torch.polar(mag, ph)
+    else:
+        x = torch.view_as_complex((2.0 * u - 1.0).view(n, 2))
+    x = x.reshape(shape).contiguous()
+    del u
+    return x
+
+
+def workload_config(shape, p, esize, args, world):
+    """The benchmark's workload: what is computed on which data (the same keys on both arms)."""
+    N = math.prod(shape)
+    prec = args.precision
+    return {"workload": f"{'x'.join(map(str, shape))} complex{'64' if esize == 8 else '128'} "
+                        + (f"({prec} split radix-16 stages) " if prec != "native" else "")
+                        + f"forward+inverse FFT, cyclic p={'x'.join(map(str, p))}",
+            "shape": list(shape), "p": list(p), "inputs": args.inputs, "seed": args.seed,
+            "l2": ("L2 flushed between steps (256 MB written); step time = sum of phase events"
+                   if args.flush_l2 else
+                   "inputs larger than L2 (129 MB); no flush" if N * esize > 129e6 else
+                   "inputs smaller than L2: L2-resident, not an HBM measurement"),
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 def oracle_cpu_run(shape, seed, reps=1):
@@ -218,28 +261,45 @@ def whole_job_value(bytes_per_rank, ms, world):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, as it stands, on the host cores, on the same workload.
+
+    Each step is one forward + inverse transform of the benchmark's own array (512^3 by default,
+    about 2.7 s on 16 Grace cores) when warm-up plus timed steps of it fit REF_BUDGET_S; otherwise
+    each step takes the largest power-of-two sub-sample that fits, and the line says so."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     shape = shape_of(args.shape)
-    sample = shape_of(args.ref_sample)
-    times, cores = [], None
-    for i in range(args.warmup + args.steps):
+    esize = 8 if args.dtype == "c64" else 16
+    p = args.p if args.p == "tune" else list(shape_of(args.p))
+    total = args.warmup + args.steps
+    t_first, cores = oracle_cpu_run(shape, args.seed)  # the first warm-up step, at the full size
+    sample = shape
+    while t_first * total > REF_BUDGET_S and math.prod(sample) > 1 << 15:
+        sample = tuple(max(1, v // 2) for v in sample)
+        t_first /= 8.0
+    times = []
+    for i in range(1, total):
         t, cores = oracle_cpu_run(sample, args.seed)
         if i >= args.warmup:
             times.append(t)
+    if not times:
+        times = [t_first]
     t = sum(times) / len(times)
-    value = 2 * alg_bytes(sample, 8) / t / 1e9
+    value = 2 * alg_bytes(sample, esize) / t / 1e9
+    same = tuple(sample) == tuple(shape)
     line = {
         "metric": METRIC, "metric_detail": METRIC_DETAIL,
         "value": value, "unit": "GB/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{'x'.join(map(str, shape))} complex64 forward+inverse FFT",
-                   "shape": list(shape), "p": args.p if args.p == "tune" else list(shape_of(args.p))},
+        "config": workload_config(shape, p, esize, args, 1),
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
-                         "sample": f"FP64 oracle forward+inverse of a {'x'.join(map(str, sample))} sample "
-                                   f"per step (seeded uniform inputs), GB/s scaled by the sample's 4*N*8 bytes"},
+                         "sample": (f"FP64 oracle (plain row-column FFT, not an optimized library) forward+inverse "
+                                    f"of the {'whole ' if same else ''}{'x'.join(map(str, sample))} array per step "
+                                    f"(seeded uniform inputs), GB/s from 4*N*{esize} bytes per transform"
+                                    + ("" if same else "; a sub-sample, the full array would not fit the budget"))},
+        "same_workload_per_step": same,
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -267,18 +327,24 @@ def run_ours(args):
     N = math.prod(shape)
     np_dtype, t_dtype = (np.complex64, torch.complex64) if args.dtype == "c64" else (np.complex128, torch.complex128)
     esize = 8 if args.dtype == "c64" else 16
-    if args.inputs == "loguniform":
-        from fftu_inputs import complex_loguniform
-        x_host = torch.from_numpy(complex_loguniform(args.seed + rank, shape, dtype=np_dtype)).pin_memory()
+    if args.inputs.startswith("device"):
+        x = device_inputs(shape, t_dtype, args.seed + rank, dev, loguniform=args.inputs == "device_loguniform")
+        x_host = None if args.no_e2e else x.cpu().pin_memory()
     else:
-        x_host = torch.from_numpy(complex_uniform(args.seed + rank, shape, dtype=np_dtype)).pin_memory()
+        if args.inputs == "loguniform":
+            from fftu_inputs import complex_loguniform
+            x_host = torch.from_numpy(complex_loguniform(args.seed + rank, shape, dtype=np_dtype)).pin_memory()
+        else:
+            x_host = torch.from_numpy(complex_uniform(args.seed + rank, shape, dtype=np_dtype)).pin_memory()
+        x = x_host.to(dev)
     prec = {"native": 0, "bf16": 1, "fp16": 2}[args.precision]
-    x = x_host.to(dev)
     y = torch.empty_like(x)
     z = torch.empty_like(x)
     t_plan = time.perf_counter()
-    fwd = fftu.Plan(shape, p, dtype=t_dtype, schedule=args.schedule, tune=tune, precision=prec)
-    inv = fftu.Plan(shape, p, dtype=t_dtype, inverse=True, schedule=args.schedule, tune=tune, precision=prec)
+    fwd = fftu.Plan(shape, p, dtype=t_dtype, schedule=args.schedule, tune=tune, precision=prec, tile=args.tile,
+                    radix=args.radix)
+    inv = fftu.Plan(shape, p, dtype=t_dtype, inverse=True, schedule=args.schedule, tune=tune, precision=prec,
+                    tile=args.tile, radix=args.radix)
     t_plan = time.perf_counter() - t_plan
     if tune:
         p = tuple(fwd.info["p"])
@@ -337,7 +403,7 @@ def run_ours(args):
 
     # parity of the timed output (round trip) so a fast wrong kernel cannot pass unnoticed
     rt_err = float((torch.linalg.vector_norm(z - x) / torch.linalg.vector_norm(x)).item())
-    vs_native = None
+    vs_native = vs_fp64 = None
     if prec:  # the same forward transform through the FP32 CUDA-core stages on the same schedule
         with fftu.Plan(shape, p, dtype=t_dtype, schedule=fftu.FFTU_SCHED_GENERIC_A) as nat:
             fftu.fftu_exec(fwd.handle, x.data_ptr(), y.data_ptr(), sh)
@@ -346,6 +412,15 @@ def run_ours(args):
             torch.cuda.synchronize(dev)
             vs_native = float((torch.linalg.vector_norm(y - y_nat) / torch.linalg.vector_norm(y_nat)).item())
             del y_nat
+        # and against an FP64 transform of the same input (cuFFT in complex128, run as a library); the
+        # element-by-element comparison with the FP64 oracle is in the test suite
+        with torch.cuda.stream(stream):
+            ref = torch.fft.fftn(x.to(torch.complex128))
+            vs_fp64 = float((torch.linalg.vector_norm(y.to(torch.complex128) - ref) /
+                             torch.linalg.vector_norm(ref)).item())
+            del ref
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
 
     # context only: the same forward + inverse through torch.fft (cuFFT), run as a library
     cufft = None
@@ -450,12 +525,16 @@ def run_ours(args):
                     "phase_frac": {"phase_a": half / (ta * 1e-3) / 1e9 / peak,
                                    "phase_b": half / (tb * 1e-3) / 1e9 / peak}}
         if esize == 16:
-            # complex128: FP64 arithmetic, not HBM, bounds the path on GB300 (1.25 TFLOP/s FP64 against
-            # 6.8 TB/s; about 5 log2 N flops per element per transform need 16 B of traffic per flop-pass)
+            # complex128: FP64 arithmetic, not HBM, bounds the path on GB300 (about 1.3 TFLOP/s FP64 against
+            # 6.7 TB/s; about 5 log2 N flops per element per transform need 16 B of traffic per flop-pass)
             gf = 2 * 5 * N * math.log2(N) / (ms_per_step * 1e-3) / 1e9
-            roofline = {"bound": "alu", "achieved": gf, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                        "frac": gf / FP64_PEAK_GFLOPS, "traffic": None, "kernel": "whole step",
-                        "peak_source": "GB300 FP64 nominal (1.25 TFLOP/s); flops counted as 5 N log2 N per transform",
+            try:
+                fp64_peak, fp64_src = fftu.fftu_measure_fp64_rate(3), "measured FP64 FMA rate on this GPU"
+            except Exception:
+                fp64_peak, fp64_src = FP64_PEAK_GFLOPS, "GB300 FP64 nominal (1.25 TFLOP/s)"
+            roofline = {"bound": "alu", "achieved": gf, "peak": fp64_peak, "unit": "GFLOP/s",
+                        "frac": gf / fp64_peak, "traffic": None, "kernel": "whole step",
+                        "peak_source": fp64_src + "; flops counted as 5 N log2 N per transform",
                         "hbm": roofline}
         serving = None
         if not args.no_serve and world == 1 and tuple(shape) == (512, 512, 512):
@@ -507,22 +586,11 @@ def run_ours(args):
             "dtype": ("f32" if esize == 8 else "f64") if not prec else
                      f"{args.precision} hi+lo tensor-core radix-16 stages, f32 elsewhere",
             "data": "synthetic",
-            "config": {"workload": f"{'x'.join(map(str, shape))} complex{'64' if esize == 8 else '128'} "
-                                   + (f"({args.precision} split radix-16 stages) " if prec else "")
-                                   + 
-                                   f"forward+inverse FFT, cyclic "
-                                   f"p={'x'.join(map(str, p))}" + (" (tuned)" if tune else ""),
-                       "shape": list(shape), "p": list(p), "schedule": fwd.info["schedule"],
-                       "precision": args.precision, "inputs": args.inputs,
-                       "p_inverse": inv.info["p"], "tuned": tune, "plan_seconds": t_plan,
-                       "strided_tile": fwd.info["tile"], "strided_radix": fwd.info["radix"],
-                       "l2": ("L2 flushed between steps (256 MB written); step time = sum of phase events"
-                              if args.flush_l2 else
-                              "inputs larger than L2 (129 MB); no flush" if N * esize > 129e6 else
-                              "inputs smaller than L2: L2-resident, not an HBM measurement"),
-                       "seed": args.seed, "inputs_recipe": f"fftu_inputs {args.inputs}, seed + rank",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "gflops_5NlogN": world * 2 * 5 * N * math.log2(N) / (ms_per_step * 1e-3) / 1e9},
+            "config": workload_config(shape, p, esize, args, world),
+            "plan": {"schedule": fwd.info["schedule"], "precision": args.precision, "p_inverse": inv.info["p"],
+                     "tuned": tune, "plan_seconds": t_plan, "strided_tile": fwd.info["tile"],
+                     "strided_radix": fwd.info["radix"]},
+            "gflops_5NlogN": world * 2 * 5 * N * math.log2(N) / (ms_per_step * 1e-3) / 1e9,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -530,17 +598,20 @@ def run_ours(args):
             "clocks": clocks,
             "round_trip_rel_l2": rt_err,
             "forward_vs_fp32_stages_rel_l2": vs_native,
+            "forward_vs_fp64_rel_l2": vs_fp64,
             "cufft_context": cufft,
             "serving": serving,
         }
-        print(json.dumps(line), flush=True)
-        if not rt_err < (1e-3 if prec != 1 else 5e-3):
-            print(f"round trip relative L2 error {rt_err:.3g}: the timed transforms are wrong", file=sys.stderr)
-            sys.exit(1)
+    err = None
+    if not rt_err < (1e-3 if prec != 1 else 5e-3):
+        err = f"round trip relative L2 error {rt_err:.3g}: the timed transforms are wrong"
     fwd.close()
     inv.close()
+    del x, y, z
+    torch.cuda.empty_cache()
     if world > 1:
         dist.destroy_process_group()
+    return (line if rank == 0 else None), err
 
 
 SERVE_SHAPES = [(32, 32, 32), (64, 64, 64), (128, 128, 128), (256, 256, 256), (1024, 1024), (2048, 2048),
@@ -796,14 +867,14 @@ def run_pointwise(args):
             "gpu_launches": args.steps * 2 * (fwd.info["launches_phase_a"] + fwd.info["launches_phase_b"]),
             "clocks": clocks,
         }
-        print(json.dumps(line), flush=True)
-        if not err < 1e-5:
-            print(f"fused and separate convolutions differ ({err:.3g})", file=sys.stderr)
-            sys.exit(1)
+    fail = None if err < 1e-5 else f"fused and separate convolutions differ ({err:.3g})"
     fwd.close()
     inv.close()
+    del x, mul, tmp, out, ref
+    torch.cuda.empty_cache()
     if world > 1:
         dist.destroy_process_group()
+    return (line if rank == 0 else None), fail
 
 
 def uneven_shapes(count, seed, cubes=False):
@@ -942,30 +1013,88 @@ def run_batch(args):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clocks,
             "round_trip_rel_l2": rt,
         }
-        print(json.dumps(line), flush=True)
-        if not rt < 1e-3:
-            print(f"round trip relative L2 error {rt:.3g}: the timed transforms are wrong", file=sys.stderr)
-            sys.exit(1)
+    fail = None if rt < 1e-3 else f"round trip relative L2 error {rt:.3g}: the timed transforms are wrong"
     fftu.fftu_batch_destroy(bf)
     fftu.fftu_batch_destroy(bi)
     for q in fwd + inv:
         q.close()
+    del xs, ys, zs
+    torch.cuda.empty_cache()
     if world > 1:
         dist.destroy_process_group()
+    return (line if rank == 0 else None), fail
+
+
+# Secondary configurations measured after the headline run, each one a short run of its own with its
+# own clock record: the other benchmark configurations, the split-precision forms and the batched and
+# fused-convolution forms, so that the default line carries every configuration's figure.
+SECONDARY = [
+    ("1024^3_c64_p16x16x8", "run", dict(shape="1024,1024,1024", p="16,16,8", steps=5, warmup=3, inputs="device")),
+    ("1024^3_c64_p8x8x8", "run", dict(shape="1024,1024,1024", p="8,8,8", steps=5, warmup=3, inputs="device")),
+    ("512^3_c64_split_bf16", "run", dict(precision="bf16", steps=10, warmup=3, inputs="device")),
+    ("512^3_c64_split_fp16", "run", dict(precision="fp16", steps=10, warmup=3, inputs="device")),
+    ("512^3_c64_split_bf16_loguniform", "run", dict(precision="bf16", steps=10, warmup=3,
+                                                    inputs="device_loguniform")),
+    ("512^3_c64_split_fp16_loguniform", "run", dict(precision="fp16", steps=10, warmup=3,
+                                                    inputs="device_loguniform")),
+    ("16384^2_c64_p16_tuned", "run", dict(shape="16384,16384", p="16,16", schedule=3, tile=4096, steps=10,
+                                          warmup=3, inputs="device")),
+    ("32^5_c64_p4", "run", dict(shape="32,32,32,32,32", p="4,4,4,4,4", tile=2048, steps=20, warmup=3,
+                                inputs="device")),
+    ("64^4_c128_p8", "run", dict(shape="64,64,64,64", p="8,8,8,8", dtype="c128", steps=10, warmup=3,
+                                 inputs="device")),
+    ("batch_64_uneven_c64", "batch", dict(batch=64, steps=20, warmup=3)),
+    ("512^3_c64_pointwise", "pointwise", dict(steps=10, warmup=3)),
+]
+SECONDARY_KEYS = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "plan", "roofline",
+                  "gflops_5NlogN", "clocks", "gpu_launches", "round_trip_rel_l2", "forward_vs_fp32_stages_rel_l2",
+                  "forward_vs_fp64_rel_l2", "per_plan_loop", "metric")
+
+
+def run_secondary(args):
+    """Every SECONDARY configuration on this GPU; a failure is reported in its entry, never dropped."""
+    import torch
+    torch.cuda.empty_cache()
+    out = {}
+    for name, kind, over in SECONDARY:
+        sub = argparse.Namespace(**vars(args))
+        sub.no_serve = sub.no_cpu_baseline = sub.no_e2e = sub.no_cufft = True
+        sub.no_secondary = True
+        for k, v in over.items():
+            setattr(sub, k, v)
+        t0 = time.perf_counter()
+        try:
+            fn = {"run": run_ours, "batch": run_batch, "pointwise": run_pointwise}[kind]
+            line, err = fn(sub)
+            ent = {k: line[k] for k in SECONDARY_KEYS if k in line}
+            if err:
+                ent["error"] = err
+        except Exception as exc:  # reported, never silently dropped
+            ent = {"error": repr(exc)}
+        ent["wall_s"] = time.perf_counter() - t0
+        out[name] = ent
+    return out
 
 
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.serve:
+        return
+    if args.serve:
         run_serve_only(args)
-    elif args.batch > 0:
-        run_batch(args)
-    elif args.pointwise:
-        run_pointwise(args)
-    else:
-        run_ours(args)
+        return
+    fn = run_batch if args.batch > 0 else run_pointwise if args.pointwise else run_ours
+    line, err = fn(args)
+    rank, world, _ = dist_env()
+    if (fn is run_ours and line is not None and world == 1 and not args.no_secondary
+            and args.shape == "512,512,512" and args.precision == "native" and args.dtype == "c64"):
+        line["secondary"] = run_secondary(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if err:
+        print(err, file=sys.stderr)
+        sys.exit(1)
 
 
 if __name__ == "__main__":

@@ -35,11 +35,14 @@ def test_reference_arm_line(monkeypatch):
     """--impl reference times the oracle and prints the contract's line (impl, cpu_baseline, e2e)."""
     monkeypatch.delenv("RANK", raising=False)
     monkeypatch.delenv("WORLD_SIZE", raising=False)
-    a = _args(["--impl", "reference", "--steps", "1", "--warmup", "3", "--ref-sample", "16,16,16"])
+    a = _args(["--impl", "reference", "--steps", "1", "--warmup", "3", "--shape", "16,16,16", "--p", "2,2,2"])
     buf = io.StringIO()
     with redirect_stdout(buf):
         bench.run_reference(a)
     line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    # the same workload and config keys the GPU arm reports for these arguments, the whole array per step
+    assert line["config"] == bench.workload_config((16, 16, 16), [2, 2, 2], 8, a, 1)
+    assert line["same_workload_per_step"] is True
     assert line["impl"] == "reference" and line["unit"] == "GB/s" and line["higher_is_better"] is True
     assert line["metric"] == bench.METRIC and line["steps"] == 1 and line["warmup"] == 3
     assert line["value"] > 0 and line["cpu_baseline"]["value"] == line["value"]
@@ -53,11 +56,25 @@ def test_reference_arm_line(monkeypatch):
 def test_reference_arm_other_ranks_print_nothing(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("WORLD_SIZE", "2")
-    a = _args(["--impl", "reference", "--ref-sample", "16,16,16"])
+    a = _args(["--impl", "reference", "--shape", "16,16,16", "--p", "2,2,2"])
     buf = io.StringIO()
     with redirect_stdout(buf):
         bench.run_reference(a)
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_subsamples_beyond_its_budget(monkeypatch):
+    """A workload whose warm-up plus timed steps would overrun the budget is timed on a sub-sample."""
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.setattr(bench, "REF_BUDGET_S", 1e-9)
+    a = _args(["--impl", "reference", "--steps", "1", "--warmup", "3", "--shape", "64,64,64", "--p", "2,2,2"])
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(a)
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    assert line["same_workload_per_step"] is False and "sub-sample" in line["cpu_baseline"]["sample"]
+    assert line["config"]["shape"] == [64, 64, 64]
 
 
 class _Done:
