@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--serve-inflight", type=int, default=0, help="0 = 2 x streams")
     ap.add_argument("--serve-piece-mib", type=int, default=0, help="host copies in pieces of this many MiB")
+    ap.add_argument("--serve-solo", type=int, default=0,
+                    help="solo (large) launches in flight at once; 0 = the server's default (one per solo stream)")
     ap.add_argument("--batch-cubes", action="store_true", help="batch of cubes n^3 only (n in 32, 64, 128)")
     ap.add_argument("--batch", type=int, default=0,
                     help="K > 0: time K uneven 3D transforms (n_l in {32, 64, 128}) in one persistent launch "
@@ -644,7 +646,7 @@ def run_serving(fftu, args, local):
         for c128 in (False, True):
             dt = np.complex128 if c128 else np.complex64
             x0 = torch.from_numpy(complex_uniform(args.seed + len(pools), shape, dtype=dt))
-            size = 6 if math.prod(shape) >= (1 << 22) else 16
+            size = 8 if math.prod(shape) >= (1 << 22) else 24 if math.prod(shape) >= (1 << 20) else 48
             slots = []
             for _ in range(size):
                 xi = torch.empty_like(x0).pin_memory()
@@ -655,7 +657,16 @@ def run_serving(fftu, args, local):
     t_alloc = time.perf_counter() - t_alloc
     cv = threading.Condition(threading.Lock())
     server = fftu.fftu_server_create(max_batch=64, streams=args.serve_streams, max_inflight=args.serve_inflight,
-                                     copy_piece_mib=args.serve_piece_mib)
+                                     copy_piece_mib=args.serve_piece_mib, max_inflight_solo=args.serve_solo)
+    # every key's instances and graphs, for every batch size, before any request is timed
+    t_warm = time.perf_counter()
+    for (shape, c128), slots in pools.items():
+        for inverse in (False, True):
+            xi, yi = slots[0]
+            fftu.fftu_server_warm(server, shape, fftu.FFTU_C128 if c128 else fftu.FFTU_C64,
+                                  fftu.FFTU_INVERSE if inverse else fftu.FFTU_FORWARD, xi.data_ptr(), yi.data_ptr(),
+                                  16)
+    t_warm = time.perf_counter() - t_warm
 
     def phase(kinds, gaps, tag0):
         """Submit kinds[i] at the cumulative gaps (None: as soon as a buffer is free); wait for all."""
@@ -717,6 +728,8 @@ def run_serving(fftu, args, local):
     timed = [c for c in done if c["tag"] >= 10 ** 6 + args.serve_warmup]
     bad = [c for c in done + sat_done if c["status"] != 0]
     lat = np.array([c["done_s"] - c["submit_s"] for c in timed]) * 1e3
+    wait = np.array([c["start_s"] - c["submit_s"] for c in timed]) * 1e3   # queued in the server
+    serve = np.array([c["done_s"] - c["start_s"] for c in timed]) * 1e3    # issued -> completion seen
     t_first = min(c["submit_s"] for c in timed)
     t_last = max(c["done_s"] for c in timed)
     span = t_last - t_first
@@ -758,10 +771,14 @@ def run_serving(fftu, args, local):
         "offered_fraction_of_saturation": rate / sat_rate,
         "achieved_rate_per_s": len(timed) / span, "p50_ms": float(np.percentile(lat, 50)),
         "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+        "queue_wait_ms": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+        "issue_to_done_ms": {"p50": float(np.percentile(serve, 50)), "p99": float(np.percentile(serve, 99))},
         "gbs_algorithmic": alg / span / 1e9, "gbs_host_copies": moved / span / 1e9,
         "failed": len(bad), "pool_stalls": stalls, "wall_s": wall, "pinned_pool_alloc_s": t_alloc,
+        "warm_s": t_warm,
         "served_vs_direct_max_rel_l2": worst, **d, "per_class": per_class,
         "server": {"streams": args.serve_streams, "max_inflight": args.serve_inflight or 2 * args.serve_streams,
+                   "max_inflight_solo": args.serve_solo or args.serve_streams - args.serve_streams // 2,
                    "max_batch": 64, "copy_piece_mib": args.serve_piece_mib},
         "mix": "shapes uniform over 32^3, 64^3, 128^3, 256^3, 1024^2, 2048^2, 4096^2; complex128 w.p. 0.1; "
                "forward/inverse equiprobable; Poisson arrivals at the offered rate (0.7 x the closed-loop "

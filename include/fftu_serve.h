@@ -3,11 +3,15 @@
  * Algorithm 2.3 with plans of fftu.h.
  *
  * A server owns one host thread and a few CUDA streams on the device that was current when it was
- * created.  Submitted requests queue per key (shape, dtype, direction).  The thread
+ * created: half of them, at the device's highest stream priority, carry batched requests, the other
+ * half, at the lowest, requests that run alone; request buffers come from the device's stream-ordered
+ * memory pool, so creating or evicting them never synchronises the device.  Submitted requests queue
+ * per key (shape, dtype, direction).  The thread
  *   - admits work against a device-memory budget (request buffers, resident plans and twiddle
  *     tables); a request that cannot fit even alone completes at once with FFTU_ERR_NOMEM,
  *     otherwise it waits until completed work frees memory;
- *   - keeps at most max_inflight launches in flight; while that many run, new requests queue;
+ *   - keeps at most max_inflight launches in flight, of them at most max_inflight_solo solo ones;
+ *     while that many run, new requests queue;
  *   - batches queued requests of one key, largest power of two first (at most max_batch), into one
  *     persistent launch (fftu_batch_*), or runs a request with N >= large_elems alone through its
  *     own plan's kernels (fftu_exec);
@@ -47,7 +51,9 @@ typedef struct {
                              arrive while the limit is reached queue, and join one launch */
     int copy_piece_mib;   /* > 0: host copies in pieces of this many MiB, one after another, so that
                              other requests' copies can run between them; 0 = one copy per array */
-    int reserved[5];      /* must be zero */
+    int max_inflight_solo; /* solo (large) launches in flight at once, 1..256; 0 = one per solo stream.
+                             More solo requests queue in the server, holding no instance */
+    int reserved[4];      /* must be zero */
 } fftu_server_config;
 
 typedef struct {
@@ -91,6 +97,19 @@ fftu_status fftu_server_create(const fftu_server_config *cfg, fftu_server *out);
 
 /* Queue one request.  Shape or type errors are returned here (nothing is queued). */
 fftu_status fftu_server_submit(fftu_server s, const fftu_request *req);
+
+/* Warm-up before a latency-sensitive stream (no counterpart in the paper): create, for the key of
+ * `like` (shape, dtype, direction), idle resident instances for every power-of-two batch size up to
+ * max_k (one batch instance of each size per batched stream; max_inflight_solo solo instances for a key
+ * with N >= large_elems), so that overlapping launches of the key each find one free, each with its
+ * device buffers, batch or plan,
+ * and, when `like`'s host buffers are page-locked, its CUDA graph.  The graphs are built with those
+ * buffers as placeholders (every replay re-points the copies), so later requests of the key replay
+ * an existing graph instead of waiting for a build.  Blocks until done, at most timeout_s seconds:
+ * FFTU_OK, FFTU_ERR_TIMEOUT, FFTU_ERR_NOMEM (the budget cannot hold the instances) or the error a
+ * request of the key would get.  No transform runs and no completion is produced; `like`'s buffers
+ * are only read as addresses.  Validation errors as for fftu_server_submit. */
+fftu_status fftu_server_warm(fftu_server s, const fftu_request *like, int max_k, double timeout_s);
 
 /* Move up to max completions into out (oldest first); returns how many, or -1 on a bad argument. */
 int fftu_server_poll(fftu_server s, fftu_completion *out, int max);

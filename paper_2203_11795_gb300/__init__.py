@@ -40,7 +40,7 @@ EXPORTS = ("fftu_plan", "fftu_plan_ex", "fftu_exec", "fftu_exec_phase", "fftu_ex
            "fftu_status_string",
            "fftu_last_error", "fftu_version",
            # include/fftu_serve.h
-           "fftu_server_create", "fftu_server_submit", "fftu_server_poll", "fftu_server_drain",
+           "fftu_server_create", "fftu_server_submit", "fftu_server_warm", "fftu_server_poll", "fftu_server_drain",
            "fftu_server_stats_get", "fftu_server_destroy")
 
 
@@ -70,7 +70,7 @@ class fftu_info(ctypes.Structure):
 class fftu_server_config(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int), ("streams", ctypes.c_int),
                 ("large_elems", ctypes.c_int64), ("use_graphs", ctypes.c_int), ("max_inflight", ctypes.c_int),
-                ("copy_piece_mib", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("copy_piece_mib", ctypes.c_int), ("max_inflight_solo", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class fftu_request(ctypes.Structure):
@@ -127,6 +127,7 @@ def _load_library() -> ctypes.CDLL:
     lib.fftu_server_submit.argtypes = [h, ctypes.POINTER(fftu_request)]
     lib.fftu_server_poll.argtypes = [h, ctypes.POINTER(fftu_completion), ctypes.c_int]
     lib.fftu_server_drain.argtypes = [h, ctypes.c_double]
+    lib.fftu_server_warm.argtypes = [h, ctypes.POINTER(fftu_request), ctypes.c_int, ctypes.c_double]
     lib.fftu_server_stats_get.argtypes = [h, ctypes.POINTER(fftu_server_stats)]
     lib.fftu_server_destroy.argtypes = [h]
     lib.fftu_status_string.argtypes = [ctypes.c_int]
@@ -139,7 +140,7 @@ def _load_library() -> ctypes.CDLL:
                  "fftu_batch_exec", "fftu_batch_check_status", "fftu_batch_destroy", "fftu_wisdom_export",
                  "fftu_wisdom_import", "fftu_wisdom_forget", "fftu_workspace_size", "fftu_set_workspace",
                  "fftu_selftest_bounded_wait", "fftu_measure_fp64_rate",
-                 "fftu_server_create", "fftu_server_submit",
+                 "fftu_server_create", "fftu_server_submit", "fftu_server_warm",
                  "fftu_server_poll", "fftu_server_drain", "fftu_server_stats_get", "fftu_server_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
@@ -276,10 +277,12 @@ def fftu_wisdom_forget() -> None:
 
 
 def fftu_server_create(device_bytes: int = 0, max_batch: int = 0, streams: int = 0, large_elems: int = 0,
-                       use_graphs: bool = True, max_inflight: int = 0, copy_piece_mib: int = 0) -> int:
+                       use_graphs: bool = True, max_inflight: int = 0, copy_piece_mib: int = 0,
+                       max_inflight_solo: int = 0) -> int:
     cfg = fftu_server_config(device_bytes=int(device_bytes), max_batch=int(max_batch), streams=int(streams),
                              large_elems=int(large_elems), use_graphs=int(bool(use_graphs)),
-                             max_inflight=int(max_inflight), copy_piece_mib=int(copy_piece_mib))
+                             max_inflight=int(max_inflight), copy_piece_mib=int(copy_piece_mib),
+                             max_inflight_solo=int(max_inflight_solo))
     h = ctypes.c_void_p()
     _check(_lib.fftu_server_create(ctypes.byref(cfg), ctypes.byref(h)), "fftu_server_create")
     return h.value
@@ -291,6 +294,16 @@ def fftu_server_submit(server: int, n, dtype: int, direction: int, in_ptr: int, 
     for i, v in enumerate(n):
         r.n[i] = v
     _check(_lib.fftu_server_submit(server, ctypes.byref(r)), "fftu_server_submit")
+
+
+def fftu_server_warm(server: int, n, dtype: int, direction: int, in_ptr: int, out_ptr: int, max_k: int,
+                     timeout_s: float = 120.0) -> None:
+    """Pre-build the key's resident instances and graphs for batch sizes up to max_k (fftu_serve.h)."""
+    n = [int(v) for v in n]
+    r = fftu_request(d=len(n), dtype=int(dtype), dir=int(direction), in_=in_ptr, out=out_ptr, tag=0)
+    for i, v in enumerate(n):
+        r.n[i] = v
+    _check(_lib.fftu_server_warm(server, ctypes.byref(r), int(max_k), float(timeout_s)), "fftu_server_warm")
 
 
 def fftu_server_poll(server: int, max_items: int = 1024) -> list:

@@ -16,6 +16,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdint>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -49,9 +50,23 @@ struct Key {
     }
 };
 
+struct WarmJob;
+
 struct Req {
     fftu_request r;
     double t_submit = 0;
+    std::shared_ptr<WarmJob> warm;  // set: not a transform but a warm-up of the key (fftu_server_warm)
+};
+
+// A warm-up request: create the key's instances for every batch size up to max_k and their graphs,
+// then signal the waiting caller.
+struct WarmJob {
+    int max_k = 1;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool done = false;
+    fftu_status status = FFTU_OK;
+    int prepared = 0;
 };
 
 struct KeyState;
@@ -126,6 +141,7 @@ struct fftu_server_st {
     std::vector<GraphBuild *> b_done;
     bool b_stop = false;
     cudaStream_t b_stream = nullptr;
+    cudaStream_t w_stream = nullptr;  // graphs built by fftu_server_warm on the server thread
 
     std::map<Key, std::unique_ptr<KeyState>> keys;  // server thread only
     size_t used = 0;
@@ -201,7 +217,8 @@ void destroy_instance(fftu_server_st *S, Instance *in) {
     if (in->batch) fftu_batch_destroy(in->batch);
     if (in->own_plan) fftu_destroy(in->own_plan);
     if (in->done) cudaEventDestroy(in->done);
-    if (in->dev) cudaFree(in->dev);
+    // stream-ordered: freed after the instance's last use on its stream, without a device-wide wait
+    if (in->dev) cudaFreeAsync(in->dev, in->stream);
     S->used -= in->bytes;
 }
 
@@ -303,8 +320,21 @@ Instance *new_instance_impl(fftu_server_st *S, KeyState *ks, int k, bool large, 
         if (in->own_plan) fftu_destroy(in->own_plan);
         return nullptr;
     }
-    if (cudaMalloc(&in->dev, 2 * (size_t)k * in->slot_bytes) != cudaSuccess) {
+    // solo (large) requests get their own low-priority streams, so that a small batch never waits in a
+    // stream behind a large request's copies and its blocks are scheduled first
+    const int ns = (int)S->streams.size();
+    if (large && S->split < ns) {
+        in->stream = S->streams[S->split + S->next_large];
+        S->next_large = (S->next_large + 1) % (ns - S->split);
+    } else {
+        in->stream = S->streams[S->next_small];
+        S->next_small = (S->next_small + 1) % (S->split > 0 ? S->split : ns);
+    }
+    // stream-ordered allocation from the device's memory pool: no device-wide synchronisation when an
+    // instance is created or evicted
+    if (cudaMallocAsync(&in->dev, 2 * (size_t)k * in->slot_bytes, in->stream) != cudaSuccess) {
         cudaGetLastError();
+        in->dev = nullptr;
         if (in->own_plan) fftu_destroy(in->own_plan);
         return nullptr;
     }
@@ -312,7 +342,7 @@ Instance *new_instance_impl(fftu_server_st *S, KeyState *ks, int k, bool large, 
         std::vector<fftu_handle> hs(k, ks->plan);
         fftu_status st = fftu_batch_create(k, hs.data(), &in->batch);
         if (st != FFTU_OK) {
-            cudaFree(in->dev);
+            cudaFreeAsync(in->dev, in->stream);
             if (st == FFTU_ERR_UNSUPPORTED) {
                 ks->solo = true;  // e.g. long lines: phase A alternates with a workspace
                 return nullptr;   // the caller retries as a solo request
@@ -322,16 +352,6 @@ Instance *new_instance_impl(fftu_server_st *S, KeyState *ks, int k, bool large, 
         }
     }
     cudaEventCreateWithFlags(&in->done, cudaEventDisableTiming);
-    // solo (large) requests get their own streams, so that a small batch never waits in a stream
-    // behind a large request's copies
-    const int ns = (int)S->streams.size();
-    if (large && S->split < ns) {
-        in->stream = S->streams[S->split + S->next_large];
-        S->next_large = (S->next_large + 1) % (ns - S->split);
-    } else {
-        in->stream = S->streams[S->next_small];
-        S->next_small = (S->next_small + 1) % (S->split > 0 ? S->split : ns);
-    }
     in->bytes = bytes;
     S->used += bytes;
     Instance *raw = in.get();
@@ -582,13 +602,20 @@ bool dispatch(fftu_server_st *S) {
     std::sort(order.begin(), order.end(),
               [](const KeyState *a, const KeyState *b) { return a->pending.front().t_submit < b->pending.front().t_submit; });
     bool any = false;
-    int inflight = 0;
+    int inflight = 0, inflight_large = 0;
     for (auto &kv : S->keys)
-        for (auto &in : kv.second->inst) inflight += in->busy ? 1 : 0;
+        for (auto &in : kv.second->inst) {
+            inflight += in->busy ? 1 : 0;
+            inflight_large += in->busy && in->large ? 1 : 0;
+        }
+    // at most max_inflight_solo solo launches: more would only queue inside the solo streams (holding
+    // instances, deepening the device's queue and delaying the small requests' copies); they wait here
+    const int large_cap = S->cfg.max_inflight_solo;
     for (KeyState *ks : order) {
         if (ks->N >= S->cfg.large_elems) ks->solo = true;
         while (!ks->pending.empty() && inflight < S->cfg.max_inflight) {
             const bool large = ks->solo;
+            if (large && inflight_large >= large_cap) break;
             const int k = large ? 1 : pow2_floor(std::min<int>((int)ks->pending.size(), S->cfg.max_batch));
             Instance *in = nullptr;
             for (auto &c : ks->inst)
@@ -613,11 +640,78 @@ bool dispatch(fftu_server_st *S) {
             ks->pending.erase(ks->pending.begin(), ks->pending.begin() + k);
             launch(S, in);
             inflight += in->busy ? 1 : 0;
+            inflight_large += in->busy && large ? 1 : 0;
             any = true;
         }
     }
     update_bytes(S);
     return any;
+}
+
+// Warm-up of one key on the server thread: an idle instance for every power-of-two batch size up to
+// the job's max_k (one solo instance for large keys) and its graph, built here on the server's warm
+// stream with the request's host buffers as placeholders (every replay re-points the copies).
+void warm_key(fftu_server_st *S, KeyState *ks, const Req &q) {
+    WarmJob &job = *q.warm;
+    fftu_status status = FFTU_OK;
+    int prepared = 0;
+    if (ks->N >= S->cfg.large_elems) ks->solo = true;
+    const int kmax = ks->solo ? 1 : std::max(1, std::min(job.max_k, S->cfg.max_batch));
+    for (int k = 1, copy = 0; k <= kmax && status == FFTU_OK;) {
+        const bool large = ks->solo;
+        // an instance runs one launch at a time, so launches of one key that overlap each take their own:
+        // one batch instance of each size per batched stream, max_inflight_solo solo instances
+        const int copies = large ? S->cfg.max_inflight_solo : std::max(1, S->split);
+        Instance *in = nullptr;
+        int have = 0;
+        for (auto &c : ks->inst)
+            if (c->k == k && c->large == large && have++ == copy) in = c.get();
+        fftu_status err = FFTU_OK;
+        if (!in) in = new_instance(S, ks, k, large, &err);
+        if (!in) {
+            if (!large && ks->solo) {  // not batchable: warm the solo path instead
+                k = 1;
+                copy = 0;
+                continue;
+            }
+            status = err != FFTU_OK ? err : FFTU_ERR_NOMEM;
+            break;
+        }
+        if (S->cfg.use_graphs && !in->gexec && !in->graph_failed && !in->building && page_locked(q.r.in) &&
+            page_locked(q.r.out)) {
+            GraphBuild b;
+            b.in = in;
+            b.hin.assign(in->k, q.r.in);
+            b.hout.assign(in->k, q.r.out);
+            build_graph(b, S->w_stream);
+            if (b.ok) {
+                in->graph = b.graph;
+                in->gexec = b.gexec;
+                in->h2d = std::move(b.h2d);
+                in->d2h = std::move(b.d2h);
+                std::lock_guard<std::mutex> lk(S->stats_mu);
+                S->stats.graph_builds++;
+            } else {
+                in->graph_failed = true;
+                note_cuda_error(S, b.error, 6);
+            }
+        }
+        ++prepared;
+        if (++copy == copies) {
+            copy = 0;
+            if (large) break;
+            k *= 2;
+        }
+    }
+    update_bytes(S);
+    {
+        std::lock_guard<std::mutex> lk(job.mu);
+        job.status = status;
+        job.prepared = prepared;
+        job.done = true;
+    }
+    job.cv.notify_all();
+    S->outstanding.fetch_sub(1);
 }
 
 void intake(fftu_server_st *S, std::deque<Req> &batch) {
@@ -636,6 +730,10 @@ void intake(fftu_server_st *S, std::deque<Req> &batch) {
             it = S->keys.emplace(k, std::move(ks)).first;
         }
         KeyState *ks = it->second.get();
+        if (q.warm) {
+            warm_key(S, ks, q);
+            continue;
+        }
         // a request that cannot fit even alone is refused at once (a plan's workspace is at most
         // N elements, its twiddle tables sum_l n_l elements)
         const size_t slot = ((size_t)ks->N * ks->esize + 255) / 256 * 256;
@@ -764,6 +862,28 @@ void server_main(fftu_server_st *S) {
     S->keys.clear();
 }
 
+// Shape, type and direction checks shared by fftu_server_submit and fftu_server_warm.
+fftu_status check_request(const fftu_request *req) {
+    if (req->d < 1 || req->d > FFTU_MAX_DIMS || (req->dtype != FFTU_C64 && req->dtype != FFTU_C128) ||
+        (req->dir != FFTU_FORWARD && req->dir != FFTU_INVERSE)) {
+        fftu::record_error("server: bad d, dtype or direction");
+        return FFTU_ERR_ARG;
+    }
+    int64_t N = 1;
+    for (int l = 0; l < req->d; ++l) {
+        if (req->n[l] < 1 || (req->n[l] & (req->n[l] - 1))) {
+            fftu::record_error("server: every n_l must be a power of two");
+            return req->n[l] < 1 ? FFTU_ERR_ARG : FFTU_ERR_UNSUPPORTED;
+        }
+        if (req->n[l] > ((int64_t)1 << 40) || N > ((int64_t)1 << 40) / req->n[l]) {  // the plans' limit
+            fftu::record_error("server: N exceeds 2^40 elements");
+            return FFTU_ERR_ARG;
+        }
+        N *= req->n[l];
+    }
+    return FFTU_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -774,7 +894,7 @@ fftu_status fftu_server_create(const fftu_server_config *cfg, fftu_server *out) 
     fftu_server_config c;
     std::memset(&c, 0, sizeof(c));
     if (cfg) c = *cfg;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
         if (c.reserved[i]) {
             fftu::record_error("server: reserved config fields must be zero");
             return FFTU_ERR_ARG;
@@ -783,10 +903,12 @@ fftu_status fftu_server_create(const fftu_server_config *cfg, fftu_server *out) 
     if (c.streams == 0) c.streams = 4;
     if (c.large_elems == 0) c.large_elems = 1ll << 22;
     if (c.max_inflight == 0) c.max_inflight = 2 * c.streams;
+    if (c.max_inflight_solo == 0) c.max_inflight_solo = c.streams >= 2 ? c.streams - c.streams / 2 : c.streams;
     if (c.max_batch < 1 || c.max_batch > 128 || c.streams < 1 || c.streams > 16 || c.large_elems < 1 ||
-        c.device_bytes < 0 || c.max_inflight < 1 || c.max_inflight > 256 || c.copy_piece_mib < 0) {
-        fftu::record_error("server: max_batch must be in [1, 128], streams in [1, 16], max_inflight in [1, 256], "
-                           "large_elems >= 1");
+        c.device_bytes < 0 || c.max_inflight < 1 || c.max_inflight > 256 || c.copy_piece_mib < 0 ||
+        c.max_inflight_solo < 1 || c.max_inflight_solo > 256) {
+        fftu::record_error("server: max_batch must be in [1, 128], streams in [1, 16], max_inflight and "
+                           "max_inflight_solo in [1, 256], large_elems >= 1");
         return FFTU_ERR_ARG;
     }
     auto S = new (std::nothrow) fftu_server_st();
@@ -810,9 +932,18 @@ fftu_status fftu_server_create(const fftu_server_config *cfg, fftu_server *out) 
     std::memset(&S->stats, 0, sizeof(S->stats));
     S->stats.budget_bytes = c.device_bytes;
     S->t0 = Clock::now();
+    // batched (small) requests on the highest stream priority, solo (large) ones on the lowest: when
+    // both have work pending, the small requests' blocks are scheduled first
+    int prio_low = 0, prio_high = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+        cudaGetLastError();
+        prio_low = prio_high = 0;
+    }
+    const int split = c.streams >= 2 ? c.streams / 2 : c.streams;
     for (int i = 0; i < c.streams; ++i) {
         cudaStream_t s;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, i < split ? prio_high : prio_low) !=
+            cudaSuccess) {
             cudaGetLastError();
             for (auto x : S->streams) cudaStreamDestroy(x);
             delete S;
@@ -820,10 +951,12 @@ fftu_status fftu_server_create(const fftu_server_config *cfg, fftu_server *out) 
         }
         S->streams.push_back(s);
     }
-    S->split = c.streams >= 2 ? c.streams / 2 : c.streams;
-    if (cudaStreamCreateWithFlags(&S->b_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    S->split = split;
+    if (cudaStreamCreateWithFlags(&S->b_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S->w_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         for (auto x : S->streams) cudaStreamDestroy(x);
+        if (S->b_stream) cudaStreamDestroy(S->b_stream);
         delete S;
         return FFTU_ERR_CUDA;
     }
@@ -833,25 +966,32 @@ fftu_status fftu_server_create(const fftu_server_config *cfg, fftu_server *out) 
     return FFTU_OK;
 }
 
+fftu_status fftu_server_warm(fftu_server S, const fftu_request *like, int max_k, double timeout_s) {
+    if (!S || !like || !like->in || !like->out || max_k < 1) return FFTU_ERR_ARG;
+    fftu_status st = check_request(like);
+    if (st != FFTU_OK) return st;
+    Req q;
+    q.r = *like;
+    q.t_submit = S->now();
+    q.warm = std::make_shared<WarmJob>();
+    q.warm->max_k = max_k;
+    auto job = q.warm;
+    S->outstanding.fetch_add(1);
+    {
+        std::lock_guard<std::mutex> lk(S->in_mu);
+        S->inbox.push_back(q);
+    }
+    S->in_cv.notify_one();
+    std::unique_lock<std::mutex> lk(job->mu);
+    if (!job->cv.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] { return job->done; }))
+        return FFTU_ERR_TIMEOUT;
+    return job->status;
+}
+
 fftu_status fftu_server_submit(fftu_server S, const fftu_request *req) {
     if (!S || !req || !req->in || !req->out) return FFTU_ERR_ARG;
-    if (req->d < 1 || req->d > FFTU_MAX_DIMS || (req->dtype != FFTU_C64 && req->dtype != FFTU_C128) ||
-        (req->dir != FFTU_FORWARD && req->dir != FFTU_INVERSE)) {
-        fftu::record_error("server: bad d, dtype or direction");
-        return FFTU_ERR_ARG;
-    }
-    int64_t N = 1;
-    for (int l = 0; l < req->d; ++l) {
-        if (req->n[l] < 1 || (req->n[l] & (req->n[l] - 1))) {
-            fftu::record_error("server: every n_l must be a power of two");
-            return req->n[l] < 1 ? FFTU_ERR_ARG : FFTU_ERR_UNSUPPORTED;
-        }
-        if (req->n[l] > ((int64_t)1 << 40) || N > ((int64_t)1 << 40) / req->n[l]) {  // the plans' limit
-            fftu::record_error("server: N exceeds 2^40 elements");
-            return FFTU_ERR_ARG;
-        }
-        N *= req->n[l];
-    }
+    const fftu_status cst = check_request(req);
+    if (cst != FFTU_OK) return cst;
     Req q;
     q.r = *req;
     q.t_submit = S->now();
@@ -903,6 +1043,7 @@ fftu_status fftu_server_destroy(fftu_server S) {
     if (S->thread.joinable()) S->thread.join();
     for (auto s : S->streams) cudaStreamDestroy(s);
     if (S->b_stream) cudaStreamDestroy(S->b_stream);
+    if (S->w_stream) cudaStreamDestroy(S->w_stream);
     delete S;
     return FFTU_OK;
 }

@@ -137,3 +137,43 @@ def test_long_line_key_falls_back_to_solo(fftu):
     reqs = [((32768,), np.complex64, False, 900), ((32768,), np.complex64, True, 901)]
     outs, done, stats = run_server(fftu, reqs)
     check_against_oracle(reqs, outs, done)
+
+
+def test_warm_prebuilds_instances_and_graphs(fftu):
+    """After fftu_server_warm, requests of the key replay graphs that already exist: no instance is
+    created and no graph is built while they run, and every result still matches the oracle."""
+    import torch
+    shape, dt = (64, 32, 16), np.complex64
+    x0 = torch.from_numpy(complex_uniform(1, shape, dtype=dt)).pin_memory()
+    y0 = torch.empty_like(x0).pin_memory()
+    s = fftu.fftu_server_create(max_batch=8, max_inflight=1)
+    try:
+        for inverse in (False, True):
+            fftu.fftu_server_warm(s, shape, fftu.FFTU_C64, fftu.FFTU_INVERSE if inverse else fftu.FFTU_FORWARD,
+                                  x0.data_ptr(), y0.data_ptr(), 8)
+        warm = fftu.fftu_server_stats_get(s)
+        # batch sizes 1, 2, 4, 8, one instance per batched stream (2 of the default 4), both directions
+        assert warm["instances"] == 2 * 4 * 2 and warm["graph_builds"] == 2 * 4 * 2 and warm["completed"] == 0
+        reqs = [(shape, dt, bool(i % 2), 1100 + i) for i in range(24)]
+        bufs = {}
+        for _, _, inverse, seed in reqs:
+            x = torch.from_numpy(complex_uniform(seed, shape, dtype=dt)).pin_memory()
+            bufs[seed] = (x, torch.empty_like(x).pin_memory())
+        for _, _, inverse, seed in reqs:
+            x, y = bufs[seed]
+            fftu.fftu_server_submit(s, shape, fftu.FFTU_C64, fftu.FFTU_INVERSE if inverse else fftu.FFTU_FORWARD,
+                                    x.data_ptr(), y.data_ptr(), seed)
+        fftu.fftu_server_drain(s, 60.0)
+        done = fftu.fftu_server_poll(s, 64)
+        after = fftu.fftu_server_stats_get(s)
+    finally:
+        fftu.fftu_server_destroy(s)
+    assert after["instance_creations"] == warm["instance_creations"]
+    assert after["graph_builds"] == warm["graph_builds"] and after["graph_replays"] == after["batches"]
+    check_against_oracle(reqs, {tag: bufs[tag][1].numpy() for tag in bufs}, done)
+    with pytest.raises(fftu.FFTUError):  # max_k < 1
+        s2 = fftu.fftu_server_create()
+        try:
+            fftu.fftu_server_warm(s2, shape, fftu.FFTU_C64, fftu.FFTU_FORWARD, x0.data_ptr(), y0.data_ptr(), 0)
+        finally:
+            fftu.fftu_server_destroy(s2)
