@@ -31,12 +31,21 @@ constexpr int kAxisThreads = 512;
 // tensor-core radix-16 stages, complex64 only), R0 is the radix of the last, CUDA-core stage.
 template <typename C, int DIR, int R0, int TCK = 0>
 __global__ void __launch_bounds__(kAxisThreads) axis_pass_kernel(const __grid_constant__ AxisPass a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
     const C *__restrict__ src = static_cast<const C *>(a.src);
     C *__restrict__ dst = static_cast<C *>(a.dst);
     const C *__restrict__ tw = static_cast<const C *>(a.tw);
-    for (int64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) axis_tile<C, DIR, R0, TCK>(a, t, sm, src, dst, tw);
+    if constexpr (TCK == 1 || TCK == 2) {
+        // tensor-core stages: operand tiles after the tile (128-byte aligned), TMEM for the block
+        const uint32_t base = (uint32_t)__cvta_generic_to_shared(smem_raw + (size_t)a.tile * sizeof(C));
+        unsigned char *raw = smem_raw + (size_t)a.tile * sizeof(C) + ((128 - (base & 127)) & 127);
+        UmmaCtx u = umma_setup<DIR, TCK>(raw, reinterpret_cast<const float2 *>(tw), a.nl, a.status);
+        for (int64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) axis_tile<C, DIR, R0, TCK>(a, t, sm, src, dst, tw, &u);
+        umma_teardown(u);
+    } else {
+        for (int64_t t = blockIdx.x; t < a.tiles; t += gridDim.x) axis_tile<C, DIR, R0, TCK>(a, t, sm, src, dst, tw);
+    }
 }
 
 // w_n^e = exp(-2 pi i e / n) for e in [n], evaluated in FP64 by sincospi on the
@@ -72,7 +81,7 @@ void launch_axis_tc(const AxisPass &a, unsigned grid, size_t smem, cudaStream_t 
 
 template <typename C, int DIR>
 cudaError_t launch_axis_t(const AxisPass &a, cudaStream_t st) {
-    size_t smem = (size_t)a.tile * sizeof(C);
+    size_t smem = axis_pass_smem_bytes(a, sizeof(C) == 16);
     int64_t grid = a.tiles < (int64_t)1 << 30 ? a.tiles : (int64_t)1 << 30;
     if (a.tc == 3) {
         launch_axis_tc<C, DIR, 3>(a, (unsigned)grid, smem, st);
@@ -130,7 +139,9 @@ cudaError_t prepare_axis_t() {
 }  // namespace
 
 size_t axis_pass_smem_bytes(const AxisPass &a, int is_double) {
-    return (size_t)a.tile * (is_double ? sizeof(double2) : sizeof(float2));
+    const size_t tile = (size_t)a.tile * (is_double ? sizeof(double2) : sizeof(float2));
+    if (!is_double && (a.tc == 1 || a.tc == 2)) return (tile + 127) / 128 * 128 + umma_smem_bytes(a.threads);
+    return tile;
 }
 
 cudaError_t launch_axis_pass(const AxisPass &a, int is_double, int dir, cudaStream_t st) {

@@ -199,6 +199,7 @@ fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPa
     if (th > 512) th = 512;
     a.threads = th;
     a.tw = pl.table(l);
+    a.status = pl.dstatus;
     a.scale = scale;
     // tc: 1 / 2 split-precision tensor-core radix-16 stages, 3 CUDA-core radix-16 stages, 0 radix 8
     a.tc = pl.precision ? pl.precision : (pl.radix == 16 ? 3 : 0);

@@ -45,7 +45,8 @@ struct AxisPass {
     int radix[kMaxStages];
     int64_t tiles;
     int tc;           // 0: radix 8 after a smaller first stage; 1 / 2: radix-16 stages as split bfloat16 /
-                      // float16 MMAs; 3: radix-16 CUDA-core stages; (1-3: the remaining factor last)
+                      // float16 tcgen05 MMAs; 3: radix-16 CUDA-core stages; (1-3: the remaining factor last)
+    int *status;      // plan status word (bounded waits of the tensor-core stages), may be NULL
 };
 
 // Phase B on the d-dim groups {m + s' (n/p)} with every p_l <= 16, in one pass.

@@ -8,6 +8,7 @@
 
 #include "fft_device.cuh"
 #include "fftu_internal.h"
+#include "umma16.cuh"
 
 namespace fftu {
 
@@ -90,217 +91,14 @@ __device__ __forceinline__ void stockham_stage(C *sm, const C *__restrict__ tw, 
     __syncthreads();
 }
 
-// ---- split-precision tensor-core radix-16 stage (complex64 only) ---------------------------------
-//
-// A radix-16 DFT of 8 butterflies is one real contraction: with X the 16 x 8 inputs (after their
-// twiddles) and F the 16-point DFT matrix, Y = F X is, in real form,
-//     [Y_re; Y_im] = [[F_re, -F_im], [F_im, F_re]] [X_re; X_im],
-// four 16 x 16 x 8 products, each one mma.sync.m16n8k16 with FP32 accumulation.  Operands are split
-// as v = v_hi + v_lo in the 16-bit type (TCK 1: bfloat16, TCK 2: float16) and the product is taken
-// as F_hi X_hi + F_hi X_lo + F_lo X_hi (the F_lo X_lo term is dropped): three MMAs per product.
-// For float16 the inputs of each group of 8 butterflies are first scaled by a power of two that
-// brings their largest magnitude into [2^13, 2^14), so that neither part leaves float16's range.
-//
-// Fragment layouts (PTX m16n8k16, A row-major 16 x 16, B column-major 16 x 8, lane = 4 g + t):
-//   A: a0 (row g, cols 2t, 2t+1), a1 (row g+8, same cols), a2 (row g, cols 2t+8, 2t+9), a3 (row g+8, ...)
-//   B: b0 (rows 2t, 2t+1; col g), b1 (rows 2t+8, 2t+9; col g)
-//   D: d0, d1 (row g; cols 2t, 2t+1), d2, d3 (row g+8; same cols)
-
-template <int TCK> __device__ __forceinline__ unsigned pack_lo_hi(float a, float b) {
-    if constexpr (TCK == 1) {
-        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        return *reinterpret_cast<unsigned *>(&h);
-    } else {
-        __half2 h = __floats2half2_rn(a, b);
-        return *reinterpret_cast<unsigned *>(&h);
-    }
-}
-
-template <int TCK> __device__ __forceinline__ float round16(float a) {
-    if constexpr (TCK == 1) return __bfloat162float(__float2bfloat16_rn(a));
-    else return __half2float(__float2half_rn(a));
-}
-
-// v = hi + lo for two values, packed as the 16-bit pairs an MMA fragment register holds
-template <int TCK> __device__ __forceinline__ void split_pair(float a, float b, unsigned &hi, unsigned &lo) {
-    const float ah = round16<TCK>(a), bh = round16<TCK>(b);
-    hi = pack_lo_hi<TCK>(ah, bh);
-    lo = pack_lo_hi<TCK>(a - ah, b - bh);
-}
-
-template <int TCK>
-__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-    if constexpr (TCK == 1)
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-            "{%0,%1,%2,%3};\n"
-            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-    else
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-            "{%0,%1,%2,%3};\n"
-            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// The lane's fragments of F_re, F_im and -F_im (hi and lo parts) of the 16-point DFT matrix
-// F[r][c] = w_16^{r c} (conjugated for the inverse), read from the pass's table of w_{n_l}^e
-// (w_16^j = w_{n_l}^{j n_l / 16}; 16 divides n_l whenever a radix-16 stage runs).
-template <int DIR, int TCK> struct Dft16Frags {
-    unsigned re_hi[4], re_lo[4], im_hi[4], im_lo[4], nim_hi[4], nim_lo[4];
-    __device__ __forceinline__ void init(int lane, const float2 *__restrict__ tw, int nl) {
-        const int g = lane >> 2, t = lane & 3;
-        const int step = nl >> 4;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int row = g + ((i & 1) ? 8 : 0), col = 2 * t + ((i & 2) ? 8 : 0);
-            float cr[2], ci[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const float2 w = dirw<DIR>(tw[((row * (col + h)) & 15) * step]);
-                cr[h] = w.x;
-                ci[h] = w.y;
-            }
-            split_pair<TCK>(cr[0], cr[1], re_hi[i], re_lo[i]);
-            split_pair<TCK>(ci[0], ci[1], im_hi[i], im_lo[i]);
-            split_pair<TCK>(-ci[0], -ci[1], nim_hi[i], nim_lo[i]);
-        }
-    }
-};
-
-// Position of butterfly w of a Stockham stage (see stockham_stage): input r at
-// base + (b + r per_col) js, output r at base + (o + r Ns) js.
-struct BflyPos {
-    int base, js, b, o, k;
-};
-
-__device__ __forceinline__ BflyPos bfly_pos(const AxisPass &a, int w, int lg_cols, int cols, int Ns, int lg_ns,
-                                            int R) {
-    BflyPos p;
-    const int col = w & (cols - 1);
-    p.b = w >> lg_cols;
-    if (a.contiguous) {
-        p.base = ((col >> a.lg_Gt) << a.lg_nlt) + (col & (a.Gt - 1));
-        p.js = a.Gt;
-    } else {
-        p.base = col;
-        p.js = cols;
-    }
-    p.k = p.b & (Ns - 1);
-    p.o = ((p.b >> lg_ns) << lg_ns) * R + p.k;
-    return p;
-}
-
-template <int DIR, int TCK>
-__device__ __forceinline__ void stockham_stage_tc16(float2 *sm, const float2 *__restrict__ tw, const AxisPass &a,
-                                                    int Ns, const Dft16Frags<DIR, TCK> &F) {
-    constexpr int GPW = kEptMax / 4;  // groups of 8 butterflies per warp and stage (4 outputs per lane each)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int lg_cols = a.lg_Gt + a.lg_V;
-    const int cols = 1 << lg_cols;
-    const int per_col = a.len >> 4;
-    const int total = cols * per_col;
-    const int twstep = a.nl / (Ns * 16);
-    const int lg_ns = 31 - __clz(Ns);
-    const int ngroups = (total + 7) >> 3;
-    float yr[GPW][4], yi[GPW][4];
-#pragma unroll
-    for (int q = 0; q < GPW; ++q) {
-        const int grp = warp + q * nwarps;
-        if (grp < ngroups) {  // uniform across the warp
-            const int w = grp * 8 + g;
-            float xr[4], xi[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                xr[i] = 0.f;
-                xi[i] = 0.f;
-            }
-            if (w < total) {
-                const BflyPos p = bfly_pos(a, w, lg_cols, cols, Ns, lg_ns, 16);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int r = 2 * t + (i & 1) + ((i & 2) ? 8 : 0);
-                    float2 x = sm[p.base + (p.b + r * per_col) * p.js];
-                    if (Ns > 1) x = cmul(x, dirw<DIR>(tw[r * p.k * twstep]));
-                    xr[i] = x.x;
-                    xi[i] = x.y;
-                }
-            }
-            float sc = 1.f, inv = 1.f;
-            if constexpr (TCK == 2) {
-                float m = 0.f;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) m = fmaxf(m, fmaxf(fabsf(xr[i]), fabsf(xi[i])));
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-                if (m > 0.f) {
-                    const int ex = (int)((__float_as_uint(m) >> 23) & 0xff) - 127;  // m in [2^ex, 2^(ex+1))
-                    int es = 127 + 13 - ex, ei = 127 - 13 + ex;
-                    es = es < 1 ? 1 : (es > 254 ? 254 : es);
-                    ei = ei < 1 ? 1 : (ei > 254 ? 254 : ei);
-                    sc = __uint_as_float((unsigned)es << 23);
-                    inv = __uint_as_float((unsigned)ei << 23);
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    xr[i] *= sc;
-                    xi[i] *= sc;
-                }
-            }
-            unsigned br_hi0, br_lo0, br_hi1, br_lo1, bi_hi0, bi_lo0, bi_hi1, bi_lo1;
-            split_pair<TCK>(xr[0], xr[1], br_hi0, br_lo0);
-            split_pair<TCK>(xr[2], xr[3], br_hi1, br_lo1);
-            split_pair<TCK>(xi[0], xi[1], bi_hi0, bi_lo0);
-            split_pair<TCK>(xi[2], xi[3], bi_hi1, bi_lo1);
-            float dr[4] = {0.f, 0.f, 0.f, 0.f}, di[4] = {0.f, 0.f, 0.f, 0.f};
-            // small terms first
-            mma16816<TCK>(dr, F.re_lo, br_hi0, br_hi1);
-            mma16816<TCK>(dr, F.re_hi, br_lo0, br_lo1);
-            mma16816<TCK>(dr, F.nim_lo, bi_hi0, bi_hi1);
-            mma16816<TCK>(dr, F.nim_hi, bi_lo0, bi_lo1);
-            mma16816<TCK>(dr, F.re_hi, br_hi0, br_hi1);
-            mma16816<TCK>(dr, F.nim_hi, bi_hi0, bi_hi1);
-            mma16816<TCK>(di, F.im_lo, br_hi0, br_hi1);
-            mma16816<TCK>(di, F.im_hi, br_lo0, br_lo1);
-            mma16816<TCK>(di, F.re_lo, bi_hi0, bi_hi1);
-            mma16816<TCK>(di, F.re_hi, bi_lo0, bi_lo1);
-            mma16816<TCK>(di, F.im_hi, br_hi0, br_hi1);
-            mma16816<TCK>(di, F.re_hi, bi_hi0, bi_hi1);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                yr[q][i] = dr[i] * inv;
-                yi[q][i] = di[i] * inv;
-            }
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < GPW; ++q) {
-        const int grp = warp + q * nwarps;
-        if (grp < ngroups) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {  // butterfly 2t + h, outputs r = g and g + 8
-                const int w = grp * 8 + 2 * t + h;
-                if (w < total) {
-                    const BflyPos p = bfly_pos(a, w, lg_cols, cols, Ns, lg_ns, 16);
-                    sm[p.base + (p.o + g * Ns) * p.js] = make_float2(yr[q][h], yi[q][h]);
-                    sm[p.base + (p.o + (g + 8) * Ns) * p.js] = make_float2(yr[q][2 + h], yi[q][2 + h]);
-                }
-            }
-        }
-    }
-    __syncthreads();
-}
-
 // One tile of a generic strided pass (see AxisPass): load, Stockham stages, permuted store.
 // TCK = 0: radix R0 first, then radix 8 (CUDA cores).  TCK = 1 / 2: radix-16 stages as split
-// bfloat16 / float16 tensor-core contractions, then one CUDA-core stage of radix R0 (the rest of len).
-// TCK = 3: radix-16 CUDA-core stages, then one stage of radix R0.
+// bfloat16 / float16 tcgen05 tensor-core contractions (umma16.cuh; `u` set up by the kernel), then
+// one CUDA-core stage of radix R0 (the rest of len).  TCK = 3: radix-16 CUDA-core stages, then one
+// stage of radix R0.
 template <typename C, int DIR, int R0, int TCK = 0>
 __device__ __forceinline__ void axis_tile(const AxisPass &a, int64_t t, C *sm, const C *__restrict__ src,
-                                          C *__restrict__ dst, const C *__restrict__ tw) {
+                                          C *__restrict__ dst, const C *__restrict__ tw, UmmaCtx *u = nullptr) {
     using Rl = typename real_of<C>::type;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int chunks = 1 << a.lg_chunks;  // class chunks per line
@@ -367,9 +165,7 @@ __device__ __forceinline__ void axis_tile(const AxisPass &a, int64_t t, C *sm, c
         }
     } else {
         static_assert(sizeof(C) == 8, "split-precision stages are for complex64");
-        Dft16Frags<DIR, TCK> F;
-        F.init(tid & 31, tw, a.nl);
-        for (; Ns * 16 <= a.len; Ns *= 16) stockham_stage_tc16<DIR, TCK>(sm, tw, a, Ns, F);
+        for (; Ns * 16 <= a.len; Ns *= 16) stockham_stage_umma16<DIR, TCK>(sm, tw, a, Ns, *u);
         if constexpr (R0 > 1) {
             if (Ns < a.len) stockham_stage<C, DIR, R0>(sm, tw, a, Ns, tid, nt);
         }

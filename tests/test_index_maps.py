@@ -370,3 +370,72 @@ def test_phase_b3_maps_and_data(kind, sign):
     got = emulate_phase_b3(wg, shape, kind, sign)
     want = cm.phase_b(wg, kind[:3], inverse=sign > 0)
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-12
+
+
+# ---- the tensor-core radix-16 stage (umma16.cuh): operand layout and the real form of F_16 --------
+
+def umma_off(m, k):
+    """Byte offset of (row m, k) in a K = 32 operand tile of 16-bit values (umma_off in umma16.cuh)."""
+    return (m & 7) * 16 + (m >> 3) * 512 + (k & 7) * 2 + (k >> 3) * 128
+
+
+def canonical_element(tile, m, k, start, lbo=128, sbo=512):
+    """Element (m, k) of an MMA operand read through a no-swizzle K-major descriptor at byte `start`
+    (core matrices of 8 rows x 16 bytes, next along K at lbo, next 8 rows at sbo), k within one
+    instruction's K = 16."""
+    off = start + (m % 8) * 16 + (m // 8) * sbo + (k % 8) * 2 + (k // 8) * lbo
+    return tile[off // 2]
+
+
+def bf16_round(x):
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp16"])
+@pytest.mark.parametrize("sign", [-1, 1], ids=["fwd", "inv"])
+def test_umma16_operands_compute_the_dft(kind, sign):
+    """Rows written by umma_write_row and read back through the descriptors' layout, multiplied as
+    the six MMAs do (x_hi G_hi + x_lo G_hi + x_hi G_lo, two K halves each), give the 16-point DFT
+    of every row within the split's error; every offset stays inside its 8 KB / 2 KB tile."""
+    rnd = bf16_round if kind == "bf16" else (lambda v: np.asarray(v, np.float32).astype(np.float16).astype(np.float32))
+    rows = 128
+    assert max(umma_off(m, k) for m in range(rows) for k in range(32)) + 2 <= rows * 32 * 2
+    assert max(umma_off(n, k) for n in range(32) for k in range(32)) + 2 <= 32 * 32 * 2
+    rng = np.random.default_rng(5)
+    xc = (rng.uniform(-1, 1, (rows, 16)) + 1j * rng.uniform(-1, 1, (rows, 16))).astype(np.complex64)
+    x = np.concatenate([xc.real, xc.imag], axis=1).astype(np.float32)        # rows x 32
+    kk, r = np.meshgrid(np.arange(16), np.arange(16), indexing="ij")
+    F = np.exp(sign * 2j * np.pi * ((kk * r) % 16) / 16)                      # F[k][r]
+    Gt = np.zeros((32, 32), dtype=np.float32)                                # row n of B = column n of G
+    Gt[:16, :16], Gt[:16, 16:] = F.real, -F.imag                             # y_re = F_re x_re - F_im x_im
+    Gt[16:, :16], Gt[16:, 16:] = F.imag, F.real                              # y_im = F_im x_re + F_re x_im
+
+    def tiles(v, nrows):
+        hi = rnd(v)
+        lo = rnd(v - hi)
+        out = []
+        for part in (hi, lo):
+            t = np.full(nrows * 32, np.nan, dtype=np.float32)
+            for m in range(nrows):
+                for k in range(32):
+                    t[umma_off(m, k) // 2] = part[m, k]
+            out.append(t)
+        return out
+
+    a_hi, a_lo = tiles(x, rows)
+    g_hi, g_lo = tiles(Gt, 32)
+
+    def operand(t, nrows, half):
+        return np.array([[canonical_element(t, m, k, 256 * half) for k in range(16)] for m in range(nrows)])
+
+    D = np.zeros((rows, 32), dtype=np.float64)
+    for half in (0, 1):
+        for A, B in ((a_hi, g_hi), (a_lo, g_hi), (a_hi, g_lo)):
+            D += operand(A, rows, half).astype(np.float64) @ operand(B, 32, half).astype(np.float64).T
+    y = D[:, :16] + 1j * D[:, 16:]
+    ref = (xc.astype(np.complex128) @ F.T)
+    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    u = 2.0 ** -8 if kind == "bf16" else 2.0 ** -11
+    assert err <= 12 * u * u, err
