@@ -55,7 +55,7 @@ def parse_args():
     ap.add_argument("--serve-rate", type=float, default=0.0,
                     help="offered Poisson rate, requests per second (0 = 0.7 x the measured saturation rate)")
     ap.add_argument("--serve-warmup", type=int, default=400)
-    ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--serve-streams", type=int, default=8)
     ap.add_argument("--serve-inflight", type=int, default=0, help="0 = 2 x streams")
     ap.add_argument("--serve-piece-mib", type=int, default=0, help="host copies in pieces of this many MiB")
     ap.add_argument("--serve-solo", type=int, default=0,

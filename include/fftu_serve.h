@@ -44,7 +44,7 @@ typedef struct fftu_server_st *fftu_server;
 typedef struct {
     int64_t device_bytes; /* budget for request buffers, plans and their workspaces; 0 = half the free memory */
     int max_batch;        /* requests per batched launch, 1..128; 0 = 64 */
-    int streams;          /* CUDA streams the batches are spread over, 1..16; 0 = 4 */
+    int streams;          /* CUDA streams, 1..16; 0 = 8 (half for batched requests, half for solo ones) */
     int64_t large_elems;  /* requests with N >= large_elems run alone through their own plan; 0 = 2^22 */
     int use_graphs;       /* nonzero: replay captured CUDA graphs for page-locked requests */
     int max_inflight;     /* launches in flight at once, 1..256; 0 = 2 x streams.  Requests that

@@ -214,6 +214,20 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+// The same bulk copy with an L2 eviction-priority hint.
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, unsigned bytes, uint64_t *bar,
+                                              unsigned long long pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ unsigned long long l2_first_policy() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
 // Order this thread's earlier generic-proxy acquires before its later bulk-copy reads of global memory.
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 template <int N> __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory"); }
@@ -579,6 +593,7 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
             n_unpub = 0;
         };
         bool abort = false;
+        const unsigned long long in_pol = l2_first_policy();
         constexpr bool kPrefetchTask = false;  // claim the next task one step early
         int next_t = MODE == 2 ? (kPrefetchTask ? (int)atomicAdd(task_ctr, 1u) : -1) : (int)blockIdx.x;
         for (int i = 0;; ++i) {
@@ -645,9 +660,16 @@ __global__ void __launch_bounds__(K::NT + 32, K::MINB) pipe_kernel(const __grid_
                 const float2 *plane = g.in + (size_t)(s0 + g.P0 * m0) * g.n1 * K::N2;
                 mbar_arrive_tx(full + s, K::B * K::N2 * (unsigned)sizeof(float2));
 #pragma unroll 1
-                for (int b = 0; b < K::B; ++b)
-                    bulk_g2s(dst + b * K::N2, plane + (size_t)(s1 + g.P1 * (a + K::A * b)) * K::N2,
-                             K::N2 * (unsigned)sizeof(float2), full + s);
+                for (int b = 0; b < K::B; ++b) {
+                    const float2 *row = plane + (size_t)(s1 + g.P1 * (a + K::A * b)) * K::N2;
+                    // with ring units above 16 MiB the ring competes with the input for L2: the input,
+                    // read once, goes in with evict-first priority (1024^3 at p = 16 x 16 x 8: phase A
+                    // 6.71 against 6.85 ms; no effect at 16 MiB units)
+                    if (MODE == 2 && (size_t)K::UNIT * sizeof(float2) > ((size_t)16 << 20))
+                        bulk_g2s_hint(dst + b * K::N2, row, K::N2 * (unsigned)sizeof(float2), full + s, in_pol);
+                    else
+                        bulk_g2s(dst + b * K::N2, row, K::N2 * (unsigned)sizeof(float2), full + s);
+                }
             } else {
                 const float2 *slot = g.scratch + (size_t)(MODE == 2 ? unit % g.ring : unit) * K::UNIT;
                 mbar_arrive_tx(full + s, K::TILE2 * (unsigned)sizeof(float2));

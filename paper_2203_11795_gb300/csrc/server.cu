@@ -900,7 +900,7 @@ fftu_status fftu_server_create(const fftu_server_config *cfg, fftu_server *out) 
             return FFTU_ERR_ARG;
         }
     if (c.max_batch == 0) c.max_batch = 64;
-    if (c.streams == 0) c.streams = 4;
+    if (c.streams == 0) c.streams = 8;
     if (c.large_elems == 0) c.large_elems = 1ll << 22;
     if (c.max_inflight == 0) c.max_inflight = 2 * c.streams;
     if (c.max_inflight_solo == 0) c.max_inflight_solo = c.streams >= 2 ? c.streams - c.streams / 2 : c.streams;

@@ -152,8 +152,8 @@ def test_warm_prebuilds_instances_and_graphs(fftu):
             fftu.fftu_server_warm(s, shape, fftu.FFTU_C64, fftu.FFTU_INVERSE if inverse else fftu.FFTU_FORWARD,
                                   x0.data_ptr(), y0.data_ptr(), 8)
         warm = fftu.fftu_server_stats_get(s)
-        # batch sizes 1, 2, 4, 8, one instance per batched stream (2 of the default 4), both directions
-        assert warm["instances"] == 2 * 4 * 2 and warm["graph_builds"] == 2 * 4 * 2 and warm["completed"] == 0
+        # batch sizes 1, 2, 4, 8, one instance per batched stream (4 of the default 8), both directions
+        assert warm["instances"] == 2 * 4 * 4 and warm["graph_builds"] == 2 * 4 * 4 and warm["completed"] == 0
         reqs = [(shape, dt, bool(i % 2), 1100 + i) for i in range(24)]
         bufs = {}
         for _, _, inverse, seed in reqs:
