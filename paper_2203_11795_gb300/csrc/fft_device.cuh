@@ -114,6 +114,12 @@ template <int DIR, typename C> __device__ __forceinline__ void dft16(C *v) {
         }
 }
 
+// Physical shared-memory slot of tile index i of the strided passes: bits 1-3 XORed with bits 4-6 when
+// the pass asks for it (swz = 14, contiguous passes; 0: identity).  A bijection on every 16-element group
+// that keeps the pairs (2k, 2k + 1) together, so that the class-strided accesses of contiguous lines
+// (strides of Gt elements, Gt = 4, 8, 16) spread over all 32 banks instead of piling on 2 to 8 of them.
+__device__ __forceinline__ int smi(int i, int swz) { return i ^ ((i >> 3) & swz); }
+
 template <int R, int DIR, typename C> __device__ __forceinline__ void dft_small(C *v) {
     if constexpr (R == 1) {
     } else if constexpr (R == 2) {

@@ -161,6 +161,7 @@ fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPa
     }
     a.mode = mode;
     a.contiguous = inner == 1;
+    a.swz = a.contiguous ? 14 : 0;  // class-strided accesses along contiguous lines: spread the banks
     int64_t V, Gt;
     if (nl <= maxtile) {  // whole lines: the pass can run in place
         V = target / nl;

@@ -47,6 +47,7 @@ struct AxisPass {
     int tc;           // 0: radix 8 after a smaller first stage; 1 / 2: radix-16 stages as split bfloat16 /
                       // float16 tcgen05 MMAs; 3: radix-16 CUDA-core stages; (1-3: the remaining factor last)
     int *status;      // plan status word (bounded waits of the tensor-core stages), may be NULL
+    int swz;          // shared-memory swizzle mask of the tile (14: bits 1-3 ^= bits 4-6, contiguous passes; 0: none)
 };
 
 // Phase B on the d-dim groups {m + s' (n/p)} with every p_l <= 16, in one pass.

@@ -61,7 +61,7 @@ __device__ __forceinline__ void stockham_stage(C *sm, const C *__restrict__ tw, 
             const int k = b & (Ns - 1);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                C x = sm[base + (b + r * per_col) * js];
+                C x = sm[smi(base + (b + r * per_col) * js, a.swz)];
                 if (r > 0 && Ns > 1) x = cmul(x, dirw<DIR>(tw[r * k * twstep]));
                 v[q][r] = x;
             }
@@ -85,7 +85,7 @@ __device__ __forceinline__ void stockham_stage(C *sm, const C *__restrict__ tw, 
             const int k = b & (Ns - 1);
             const int o = ((b >> lg_ns) << lg_ns) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) sm[base + (o + r * Ns) * js] = v[q][r];
+            for (int r = 0; r < R; ++r) sm[smi(base + (o + r * Ns) * js, a.swz)] = v[q][r];
         }
     }
     __syncthreads();
@@ -132,7 +132,7 @@ __device__ __forceinline__ void axis_tile(const AxisPass &a, int64_t t, C *sm, c
             }
             const int64_t gp = c0 + (lp & (a.Gt - 1)) + ((int64_t)(lp >> a.lg_Gt) << a.lg_G);
             const int64_t g = a.contiguous ? gbase + (int64_t)v * a.nl + gp : gbase + gp * a.inner + v;
-            async_copy_pair(reinterpret_cast<float2 *>(sm + e), reinterpret_cast<const float2 *>(src + g));
+            async_copy_pair(reinterpret_cast<float2 *>(sm + smi(e, a.swz)), reinterpret_cast<const float2 *>(src + g));
         }
     } else
     for (int e = tid; e < a.tile; e += nt) {
@@ -146,7 +146,7 @@ __device__ __forceinline__ void axis_tile(const AxisPass &a, int64_t t, C *sm, c
         }
         const int64_t gp = c0 + (lp & (a.Gt - 1)) + ((int64_t)(lp >> a.lg_Gt) << a.lg_G);
         const int64_t g = a.contiguous ? gbase + (int64_t)v * a.nl + gp : gbase + gp * a.inner + v;
-        async_copy(sm + e, src + g);
+        async_copy(sm + smi(e, a.swz), src + g);
     }
     async_copy_wait();
     __syncthreads();
@@ -192,16 +192,17 @@ __device__ __forceinline__ void axis_tile(const AxisPass &a, int64_t t, C *sm, c
                 const int c = c0 + cl;
                 if (a.contiguous) {  // the pair is (m, m + 1) of class c
                     const int row = v << a.lg_nlt;
-                    v0 = sm[row + cl + (m << a.lg_Gt)];
-                    v1 = sm[row + cl + ((m + 1) << a.lg_Gt)];
+                    v0 = sm[smi(row + cl + (m << a.lg_Gt), a.swz)];
+                    v1 = sm[smi(row + cl + ((m + 1) << a.lg_Gt), a.swz)];
                     if (c != 0) {
                         if (m != 0) v0 = cmul(v0, dirw<DIR>(tw[c * m]));
                         v1 = cmul(v1, dirw<DIR>(tw[c * (m + 1)]));
                     }
                 } else {  // the pair is vectors (v, v + 1) of one output position
                     const int base = ((cl + (m << a.lg_Gt)) << a.lg_V) + v;
-                    v0 = sm[base];
-                    v1 = sm[base + 1];
+                    const float4 pv = *reinterpret_cast<const float4 *>(sm + smi(base, a.swz));  // base even
+                    v0 = mk<C>(pv.x, pv.y);
+                    v1 = mk<C>(pv.z, pv.w);
                     if (c != 0 && m != 0) {
                         const C w = dirw<DIR>(tw[c * m]);
                         v0 = cmul(v0, w);
@@ -210,8 +211,9 @@ __device__ __forceinline__ void axis_tile(const AxisPass &a, int64_t t, C *sm, c
                 }
                 gp = ((int64_t)c << a.lg_len) + m;
             } else {
-                v0 = sm[e];
-                v1 = sm[e + 1];
+                const float4 pv = *reinterpret_cast<const float4 *>(sm + smi(e, a.swz));
+                v0 = mk<C>(pv.x, pv.y);
+                v1 = mk<C>(pv.z, pv.w);
                 gp = c0 + (lpo & (a.Gt - 1)) + ((int64_t)(lpo >> a.lg_Gt) << a.lg_G);
             }
             if (a.scale != 1.0) {
@@ -239,11 +241,11 @@ __device__ __forceinline__ void axis_tile(const AxisPass &a, int64_t t, C *sm, c
             const int cl = lpo >> a.lg_len, m = lpo & (a.len - 1);
             const int c = c0 + cl;
             const int src_lp = cl + (m << a.lg_Gt);
-            val = sm[a.contiguous ? (v << a.lg_nlt) + src_lp : (src_lp << a.lg_V) + v];
+            val = sm[smi(a.contiguous ? (v << a.lg_nlt) + src_lp : (src_lp << a.lg_V) + v, a.swz)];
             if (c != 0 && m != 0) val = cmul(val, dirw<DIR>(tw[c * m]));
             gp = ((int64_t)c << a.lg_len) + m;
         } else {
-            val = sm[e];
+            val = sm[smi(e, a.swz)];
             gp = c0 + (lpo & (a.Gt - 1)) + ((int64_t)(lpo >> a.lg_Gt) << a.lg_G);
         }
         if (a.scale != 1.0) val = cscale(val, scale);

@@ -246,7 +246,7 @@ __device__ __forceinline__ void stockham_stage_umma16(float2 *sm, const float2 *
         p = umma_bfly(a, w, lg_cols, cols, Ns, lg_ns);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-            float2 v = sm[p.base + (p.b + q * per_col) * p.js];
+            float2 v = sm[smi(p.base + (p.b + q * per_col) * p.js, a.swz)];
             if (Ns > 1) v = cmul(v, dirw<DIR>(tw[q * p.k * twstep]));
             x[q] = v.x;
             x[16 + q] = v.y;
@@ -314,7 +314,8 @@ __device__ __forceinline__ void stockham_stage_umma16(float2 *sm, const float2 *
     // 4. outputs in Stockham order
     if (active) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) sm[p.base + (p.o + q * Ns) * p.js] = make_float2(y[q] * inv, y[16 + q] * inv);
+        for (int q = 0; q < 16; ++q)
+            sm[smi(p.base + (p.o + q * Ns) * p.js, a.swz)] = make_float2(y[q] * inv, y[16 + q] * inv);
     }
     __syncthreads();
 }
