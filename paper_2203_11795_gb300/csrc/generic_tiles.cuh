@@ -271,6 +271,138 @@ __device__ __forceinline__ void axis_dft(C *sm, int total, int S, int tid, int n
     }
 }
 
+// F_{R1} along a stride-S axis and F_{R2} along the next (stride S R1) in one shared-memory pass: each group
+// holds the R1 x R2 values of one fixed position of the other axes in registers.
+template <typename C, int DIR, int R1, int R2>
+__device__ __forceinline__ void axis_dft2(C *sm, int total, int S, int tid, int nt) {
+    const int groups = total / (R1 * R2);
+    const int lg_s = 31 - __clz(S);
+    for (int g = tid; g < groups; g += nt) {
+        const int base = ((g >> lg_s) << lg_s) * (R1 * R2) + (g & (S - 1));
+        C v[R1 * R2];
+#pragma unroll
+        for (int r = 0; r < R1 * R2; ++r) v[r] = sm[base + r * S];
+#pragma unroll
+        for (int r2 = 0; r2 < R2; ++r2) {
+            C w[R1];
+#pragma unroll
+            for (int r1 = 0; r1 < R1; ++r1) w[r1] = v[r2 * R1 + r1];
+            dft_small<R1, DIR>(w);
+#pragma unroll
+            for (int r1 = 0; r1 < R1; ++r1) v[r2 * R1 + r1] = w[r1];
+        }
+#pragma unroll
+        for (int r1 = 0; r1 < R1; ++r1) {
+            C w[R2];
+#pragma unroll
+            for (int r2 = 0; r2 < R2; ++r2) w[r2] = v[r2 * R1 + r1];
+            dft_small<R2, DIR>(w);
+#pragma unroll
+            for (int r2 = 0; r2 < R2; ++r2) v[r2 * R1 + r1] = w[r2];
+        }
+#pragma unroll
+        for (int r = 0; r < R1 * R2; ++r) sm[base + r * S] = v[r];
+    }
+}
+
+// Offset of tile element e (e even when pairs) from the tile's base: the m_d position and the s'_l of every
+// axis (shared by all tiles; the fused phase-B kernel computes a thread's offsets once).
+__device__ __forceinline__ int64_t phaseb_offset(const PhaseBFused &b, int e) {
+    const int d = b.d;
+    const int mt = e & (b.Mt - 1);
+    int sf = e >> b.lg_Mt;
+    int64_t g = (int64_t)mt * b.stride[d - 1];
+    for (int l = d - 1; l >= 0; --l) {
+        const int sl = sf & (b.p[l] - 1);
+        sf >>= b.lg_p[l];
+        g += (int64_t)sl * b.L[l] * b.stride[l];
+    }
+    return g;
+}
+
+// Global element offset of tile t's first element (m_0 .. m_{d-2} and the first m_{d-1} of the tile).
+__device__ __forceinline__ int64_t phaseb_base(const PhaseBFused &b, int64_t t) {
+    const int d = b.d;
+    const int lg_td = b.lg_L[d - 1] - b.lg_Mt;  // tiles along the last axis (log2)
+    int64_t rem = t >> lg_td;
+    int64_t base = ((t & (((int64_t)1 << lg_td) - 1)) << b.lg_Mt) * b.stride[d - 1];
+    for (int l = d - 2; l >= 0; --l) {
+        base += (rem & (b.L[l] - 1)) * b.stride[l];
+        rem >>= b.lg_L[l];
+    }
+    return base;
+}
+
+// The DFT stages of a landed phase-B tile: F_{p_l} along every axis, last axis first, two adjacent axes per
+// shared-memory pass where p_l p_{l-1} <= 16.
+template <typename C, int DIR>
+__device__ __forceinline__ void phaseb_dfts(const PhaseBFused &b, C *sm) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int total = b.P * b.Mt;
+    int S = b.Mt;
+    for (int l = b.d - 1; l >= 0; --l) {
+        const int pp = (l > 0 && b.p[l] > 1 && b.p[l - 1] > 1) ? b.p[l] * b.p[l - 1] : 0;
+        if (pp > 0 && pp <= 16) {
+            switch (b.p[l] * 100 + b.p[l - 1]) {
+                case 202: axis_dft2<C, DIR, 2, 2>(sm, total, S, tid, nt); break;
+                case 204: axis_dft2<C, DIR, 2, 4>(sm, total, S, tid, nt); break;
+                case 208: axis_dft2<C, DIR, 2, 8>(sm, total, S, tid, nt); break;
+                case 402: axis_dft2<C, DIR, 4, 2>(sm, total, S, tid, nt); break;
+                case 404: axis_dft2<C, DIR, 4, 4>(sm, total, S, tid, nt); break;
+                case 802: axis_dft2<C, DIR, 8, 2>(sm, total, S, tid, nt); break;
+                default: break;
+            }
+            S *= pp;
+            --l;
+        } else {
+            switch (b.p[l]) {
+                case 2: axis_dft<C, DIR, 2>(sm, total, S, tid, nt); break;
+                case 4: axis_dft<C, DIR, 4>(sm, total, S, tid, nt); break;
+                case 8: axis_dft<C, DIR, 8>(sm, total, S, tid, nt); break;
+                case 16: axis_dft<C, DIR, 16>(sm, total, S, tid, nt); break;
+                default: break;
+            }
+            S *= b.p[l];
+        }
+        __syncthreads();
+    }
+}
+
+// One complex64 phase-B tile with the thread's element offsets from the tile base precomputed (16-byte
+// pairs; K pairs per thread at most): the per-element index arithmetic is one add.
+template <int DIR, int K>
+__device__ __forceinline__ void phaseb_tile_pairs(const PhaseBFused &b, int64_t t, float2 *sm, float2 *__restrict__ data,
+                                                  const int (&off)[K]) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int total = b.P * b.Mt;
+    const int64_t base = phaseb_base(b, t);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int e = 2 * (tid + k * nt);
+        if (e < total)
+            async_copy_pair(sm + e, data + base + off[k]);
+    }
+    async_copy_wait();
+    __syncthreads();
+    phaseb_dfts<float2, DIR>(b, sm);
+    const float scale = (float)b.scale;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int e = 2 * (tid + k * nt);
+        if (e < total) {
+            float4 v = *reinterpret_cast<const float4 *>(sm + e);
+            if (b.scale != 1.0) {
+                v.x *= scale;
+                v.y *= scale;
+                v.z *= scale;
+                v.w *= scale;
+            }
+            *reinterpret_cast<float4 *>(data + base + off[k]) = v;
+        }
+    }
+    __syncthreads();
+}
+
 // One tile of the generic fused phase B (see PhaseBFused): all p values for Mt consecutive m_d.
 template <typename C, int DIR>
 __device__ __forceinline__ void phaseb_tile(const PhaseBFused &b, int64_t t, C *sm, C *__restrict__ data) {
@@ -278,14 +410,7 @@ __device__ __forceinline__ void phaseb_tile(const PhaseBFused &b, int64_t t, C *
     const int tid = threadIdx.x, nt = blockDim.x;
     const int d = b.d;
     const int total = b.P * b.Mt;
-    const int lg_td = b.lg_L[d - 1] - b.lg_Mt;  // tiles along the last axis (log2)
-    // tile -> fixed m_0..m_{d-2} and the first m_{d-1}
-    int64_t rem = t >> lg_td;
-    int64_t base = ((t & (((int64_t)1 << lg_td) - 1)) << b.lg_Mt) * b.stride[d - 1];
-    for (int l = d - 2; l >= 0; --l) {
-        base += (rem & (b.L[l] - 1)) * b.stride[l];
-        rem >>= b.lg_L[l];
-    }
+    const int64_t base = phaseb_base(b, t);  // fixed m_0..m_{d-2} and the first m_{d-1}
     // complex64 with Mt >= 2: elements mt and mt + 1 are adjacent along the last axis (stride 1),
     // so loads and stores go in 16-byte pairs with one index computation per pair
     const bool pairs = sizeof(C) == 8 && b.Mt >= 2;
@@ -306,18 +431,7 @@ __device__ __forceinline__ void phaseb_tile(const PhaseBFused &b, int64_t t, C *
     }
     async_copy_wait();
     __syncthreads();
-    int S = b.Mt;
-    for (int l = d - 1; l >= 0; --l) {
-        switch (b.p[l]) {
-            case 2: axis_dft<C, DIR, 2>(sm, total, S, tid, nt); break;
-            case 4: axis_dft<C, DIR, 4>(sm, total, S, tid, nt); break;
-            case 8: axis_dft<C, DIR, 8>(sm, total, S, tid, nt); break;
-            case 16: axis_dft<C, DIR, 16>(sm, total, S, tid, nt); break;
-            default: break;
-        }
-        S *= b.p[l];
-        __syncthreads();
-    }
+    phaseb_dfts<C, DIR>(b, sm);
     const Rl scale = (Rl)b.scale;
     for (int e = tid * step; e < total; e += nt * step) {
         const int mt = e & (b.Mt - 1);

@@ -22,11 +22,30 @@ namespace fftu {
 
 namespace {
 
+constexpr int kPairsPerThread = 16;  // complex64 tiles up to 16 x 2 x 256 elements take the offset path
+
+// complex64: three CTAs of 256 threads per SM (64 KB tiles), the offsets of a thread held in 16 registers.
 template <typename C, int DIR>
-__global__ void __launch_bounds__(256) phase_b_fused_kernel(const __grid_constant__ PhaseBFused b) {
+__global__ void __launch_bounds__(256, sizeof(C) == 8 ? 3 : 1) phase_b_fused_kernel(const __grid_constant__ PhaseBFused b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
     C *__restrict__ data = static_cast<C *>(b.data);
+    if constexpr (sizeof(C) == 8) {
+        if (b.Mt >= 2 && b.P * b.Mt <= 2 * kPairsPerThread * (int)blockDim.x &&
+            phaseb_offset(b, b.P * b.Mt - 1) < (int64_t)INT32_MAX) {
+            // every tile has the same offsets from its base (the largest is the last element's): compute
+            // this thread's once, in 32 bits
+            int off[kPairsPerThread];
+#pragma unroll
+            for (int k = 0; k < kPairsPerThread; ++k) {
+                const int e = 2 * ((int)threadIdx.x + k * (int)blockDim.x);
+                off[k] = e < b.P * b.Mt ? (int)phaseb_offset(b, e) : 0;
+            }
+            for (int64_t t = blockIdx.x; t < b.tiles; t += gridDim.x)
+                phaseb_tile_pairs<DIR, kPairsPerThread>(b, t, sm, data, off);
+            return;
+        }
+    }
     for (int64_t t = blockIdx.x; t < b.tiles; t += gridDim.x) phaseb_tile<C, DIR>(b, t, sm, data);
 }
 
