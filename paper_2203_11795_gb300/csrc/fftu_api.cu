@@ -10,6 +10,7 @@
 // device status word.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -80,13 +81,14 @@ int radix_plan_tc(int len, int *radix) {
     return n;
 }
 
-enum StepKind { STEP_AXIS = 1, STEP_PHASE_B_FUSED = 2, STEP_PHASE_B3 = 3, STEP_PHASE_A3 = 4 };
+enum StepKind { STEP_AXIS = 1, STEP_PHASE_B_FUSED = 2, STEP_PHASE_B3 = 3, STEP_PHASE_A3 = 4, STEP_LINE = 5 };
 
 struct Step {
     int kind;
-    AxisPass axis;
+    AxisPass axis;  // STEP_LINE keeps the strided-pass form of the same axis (in place; batching)
     PhaseBFused pb;
     Phase3Launch a3;
+    LinePass line;
 };
 
 // Residue units up to this size run phase A as one persistent kernel through a
@@ -110,6 +112,7 @@ struct Plan {
     void *tables = nullptr;
     size_t table_bytes = 0;
     int64_t table_off[FFTU_MAX_DIMS] = {};
+    int64_t line_table_off[FFTU_MAX_DIMS] = {};  // line-pass tables (complex64, len in [256, 2048]), else -1
     void *workspace = nullptr;   // [natural schedule's part | CYCLIC layout temp], plan-owned or caller's
     size_t workspace_bytes = 0;  // bytes the plan allocated itself (0 when the caller supplies it)
     bool ws_owned = false;
@@ -125,15 +128,28 @@ struct Plan {
     std::vector<Step> phase_a, phase_b;
     std::vector<Step> phase_a_inplace;  // used when in == out and phase_a cannot run in place
     bool generic_pingpong = false;      // generic phase A alternates between out and the workspace
+    bool axis_pingpong = false;         // ... even in its strided-pass form (a line longer than the tile)
 
     const void *table(int l) const { return static_cast<const char *>(tables) + table_off[l] * esize; }
+    const void *line_table(int l) const {
+        return line_table_off[l] < 0 ? nullptr : static_cast<const char *>(tables) + line_table_off[l] * esize;
+    }
 };
+
+// Sub-FFT length of axis l's phase-A pass when the register-resident line pass serves it, else 0.
+inline int64_t line_len(const int64_t *n, const int64_t *p, int l, int dtype, int precision) {
+    if (dtype != FFTU_C64 || precision != FFTU_PREC_NATIVE) return 0;
+    const int64_t len = n[l] / p[l];
+    return (p[l] > 1 && len >= 256 && len <= 2048) ? len : 0;
+}
 
 namespace {
 
 // Whole-line tiles aim at this many elements: 256 threads of 16 (complex64) or 8 (complex128)
 // values, so that two CTAs share an SM at the kernels' register count.
 constexpr int64_t kTileTargetC64 = 4096, kTileTargetC128 = 2048;
+// Threads per CTA of a line pass (T threads per line, kLineThreads / T lines).
+constexpr int kLineThreads = 256;
 
 // Generic schedule: one strided pass per axis.  mode 0 = phase A, mode 1 = phase B.
 fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPass &a) {
@@ -245,14 +261,56 @@ bool make_phase_b_fused(const Plan &pl, double scale, PhaseBFused &b) {
     return true;
 }
 
-fftu_status build_generic_phase_a(Plan &pl, std::vector<Step> &out) {
+// The register-resident form of axis l's phase-A pass (line_pass.cu), when it serves the axis.
+bool make_line_pass(const Plan &pl, int l, LinePass &a) {
+    std::memset(&a, 0, sizeof(a));
+    const int64_t len = line_len(pl.n, pl.p, l, pl.dtype, pl.precision);
+    if (len == 0 || !pl.line_table(l)) return false;
+    int64_t outer = 1, inner = 1;
+    for (int k = 0; k < l; ++k) outer *= pl.n[k];
+    for (int k = l + 1; k < pl.d; ++k) inner *= pl.n[k];
+    a.outer = outer;
+    a.inner = inner;
+    a.nl = (int)pl.n[l];
+    a.len = (int)len;
+    a.G = (int)pl.p[l];
+    a.T = (int)(len / 16);
+    a.contiguous = inner == 1;
+    int W = kLineThreads / a.T;  // lines per CTA
+    if (a.contiguous) {
+        a.Wc = (int)std::min<int64_t>(W, a.G);
+        a.Wo = (int)std::min<int64_t>(W / a.Wc, outer);
+        W = a.Wc * a.Wo;
+        a.ctas = (outer / a.Wo) * (a.G / a.Wc);
+    } else {
+        W = (int)std::min<int64_t>(W, inner);
+        a.Wc = 1;
+        a.Wo = 1;
+        a.ctas = outer * a.G * (inner / W);
+    }
+    a.W = W;
+    a.lg_W = ilog2(W);
+    a.lg_Wc = ilog2(a.Wc);
+    a.pad = W >= 2 ? 16 / W : 0;
+    a.threads = a.T * W;
+    a.smem = (size_t)W * (size_t)(len + a.pad) * pl.esize;
+    if (a.threads < 32 || a.threads > 512 || a.smem > (size_t)kMaxDynSmem || a.ctas > 0x7fffffffll) return false;
+    a.tw = pl.table(l);
+    a.tw1 = pl.line_table(l);
+    a.tw2 = static_cast<const char *>(pl.line_table(l)) + len * pl.esize;
+    return true;
+}
+
+fftu_status build_generic_phase_a(Plan &pl, std::vector<Step> &out, bool allow_line) {
     // Contiguous axis first (reads the caller's array in long runs).
     for (int l = pl.d - 1; l >= 0; --l) {
         if (pl.n[l] == 1) continue;
         Step s;
+        std::memset(&s.line, 0, sizeof(s.line));
         s.kind = STEP_AXIS;
         fftu_status st = make_axis_pass(pl, l, 0, 1.0, s.axis);
         if (st != FFTU_OK) return st;
+        if (allow_line && make_line_pass(pl, l, s.line)) s.kind = STEP_LINE;
         out.push_back(s);
     }
     return FFTU_OK;
@@ -314,13 +372,17 @@ fftu_status build_schedule(Plan &pl, int sched) {
         if (st != FFTU_OK) return st;
     }
     {
-        fftu_status st = build_generic_phase_a(pl, fused_a ? pl.phase_a_inplace : pl.phase_a);
+        // line passes are never in place: only the plain phase-A list takes them
+        fftu_status st = build_generic_phase_a(pl, fused_a ? pl.phase_a_inplace : pl.phase_a, !fused_a);
         if (st != FFTU_OK) return st;
     }
     if (!fused_a) {
-        // a pass over part of the classes of a line is not in place: alternate with a workspace
-        for (const Step &s : pl.phase_a)
-            if (s.kind == STEP_AXIS && s.axis.Gt < s.axis.G) pl.generic_pingpong = true;
+        // a pass over part of the classes of a line, or a line pass, is not in place: alternate with a
+        // workspace
+        for (const Step &s : pl.phase_a) {
+            if (s.axis.Gt < s.axis.G) pl.axis_pingpong = true;
+            if (s.kind == STEP_LINE || s.axis.Gt < s.axis.G) pl.generic_pingpong = true;
+        }
         if (pl.generic_pingpong) pl.ws_natural = (size_t)pl.N * pl.esize;
     }
     // Phase B: one fused pass when every p_l <= 16, else one pass per axis.
@@ -401,6 +463,9 @@ fftu_status run_steps(Plan *pl, const std::vector<Step> &steps, const void *firs
             a.src = src;
             a.dst = dst;
             e = launch_axis_pass(a, is_double, pl->dir, st);
+        } else if (s.kind == STEP_LINE) {
+            record_error("internal: a line pass outside the alternating phase-A schedule");
+            return FFTU_ERR_INTERNAL;
         } else if (s.kind == STEP_PHASE_A3) {
             Phase3Launch l = s.a3;
             l.in = src;
@@ -448,7 +513,7 @@ fftu_status plan_view(fftu_handle h, PlanView *v) {
     v->dtype = pl.dtype;
     v->dir = pl.dir;
     v->device = pl.device;
-    v->pingpong = pl.generic_pingpong;
+    v->pingpong = pl.axis_pingpong;  // the batch runs the strided-pass form of every step
     v->precision = pl.precision;
     v->layout = pl.layout;
     v->radix = pl.radix;
@@ -634,11 +699,16 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
         free_plan(pl);
         return cuda_fail(e, "cudaGetDevice");
     }
-    // twiddle tables
+    // twiddle tables: w_{n_l}^e per axis, then the line-pass tables of the axes a line pass can serve
     int64_t off = 0;
     for (int l = 0; l < d; ++l) {
         pl->table_off[l] = off;
         off += n[l];
+    }
+    for (int l = 0; l < d; ++l) {
+        const int64_t len = line_len(n, pp, l, dtype, precision);
+        pl->line_table_off[l] = len ? off : -1;
+        off += len ? len + len / 16 : 0;
     }
     pl->table_bytes = (size_t)off * pl->esize;
     e = cudaMalloc(&pl->tables, pl->table_bytes);
@@ -661,9 +731,13 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
         set_err("status word allocation: %s", cudaGetErrorString(e));
         return FFTU_ERR_NOMEM;
     }
-    for (int l = 0; l < d && e == cudaSuccess; ++l)
+    for (int l = 0; l < d && e == cudaSuccess; ++l) {
         e = launch_twiddle_table(static_cast<char *>(pl->tables) + pl->table_off[l] * pl->esize, n[l],
                                  dtype == FFTU_C128, ps);
+        if (e == cudaSuccess && pl->line_table_off[l] >= 0)
+            e = launch_line_tables(static_cast<char *>(pl->tables) + pl->line_table_off[l] * pl->esize,
+                                   (int)(n[l] / pp[l]), ps);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
     cudaStreamDestroy(ps);
     if (e != cudaSuccess) {
@@ -673,6 +747,7 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
     e = prepare_axis_pass(dtype == FFTU_C128, dir);
     if (e == cudaSuccess) e = prepare_phase_b_fused(dtype == FFTU_C128, dir);
     if (e == cudaSuccess) e = prepare_phase_b3(dtype == FFTU_C128, dir);
+    if (e == cudaSuccess && dtype == FFTU_C64) e = prepare_line_pass(dir);
     if (e != cudaSuccess) {
         free_plan(pl);
         return cuda_fail(e, "kernel attributes");
@@ -723,19 +798,35 @@ namespace {
 // The transform on the natural view (every layout ends up here).
 fftu_status exec_natural(Plan *pl, fftu_phase phase, const void *in, void *out, cudaStream_t st) {
     if ((phase & FFTU_PHASE_A) && pl->generic_pingpong) {
-        // buffers: pass k (of d) writes out when d - k is even, the workspace otherwise
+        // buffers: pass k (of np) writes out when np - k is even, the workspace otherwise.  In place with
+        // np odd, the first pass runs in place on out in its strided-pass form (whole lines only).
         const int np = (int)pl->phase_a.size();
         const void *src = in;
         for (int k = 1; k <= np; ++k) {
+            const Step &s = pl->phase_a[k - 1];
             void *dst = ((np - k) % 2 == 0) ? out : pl->workspace;
-            if (dst == src) {
+            const bool whole_lines = s.axis.Gt == s.axis.G;
+            if (dst == src && !(k == 1 && whole_lines && src == out)) {
                 set_err("in-place transform with a long-line axis needs in != out");
                 return FFTU_ERR_UNSUPPORTED;
             }
-            AxisPass a = pl->phase_a[k - 1].axis;
-            a.src = src;
-            a.dst = dst;
-            cudaError_t e = launch_axis_pass(a, pl->dtype == FFTU_C128, pl->dir, st);
+            cudaError_t e;
+            if (dst == src) {  // the in-place first pass: strided form, then the alternation continues
+                AxisPass a = s.axis;
+                a.src = src;
+                a.dst = out;
+                e = launch_axis_pass(a, pl->dtype == FFTU_C128, pl->dir, st);
+            } else if (s.kind == STEP_LINE) {
+                LinePass a = s.line;
+                a.src = src;
+                a.dst = dst;
+                e = launch_line_pass(a, pl->dir, st);
+            } else {
+                AxisPass a = s.axis;
+                a.src = src;
+                a.dst = dst;
+                e = launch_axis_pass(a, pl->dtype == FFTU_C128, pl->dir, st);
+            }
             if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
             src = dst;
         }

@@ -50,6 +50,26 @@ struct AxisPass {
     int swz;          // shared-memory swizzle mask of the tile (14: bits 1-3 ^= bits 4-6, contiguous passes; 0: none)
 };
 
+// Phase-A pass along one axis with each sub-FFT held in registers (complex64; see line_pass.cu).  Same
+// operation as an AxisPass of mode 0 for sub-FFT lengths len = 16 T, T in {16, 32, 64, 128}, but never in
+// place: it reads src and writes dst.  A CTA runs W = Wc x Wo lines (contiguous axis: Wc adjacent classes
+// of Wo adjacent lines) or W adjacent inner positions (strided axis), T threads per line.
+struct LinePass {
+    const void *src;
+    void *dst;
+    const void *tw;    // w_{nl}^e, e in [nl] (forward roots)
+    const void *tw1;   // w_len^{(j k1) mod len} at k1 T + j, k1 in [16], j in [T]
+    const void *tw2;   // w_T^{(j1 k2) mod T} at j1 16 + k2, j1 in [T / 16], k2 in [16]
+    int64_t outer, inner;
+    int nl, len, G, T;
+    int contiguous;
+    int W, lg_W, Wc, lg_Wc, Wo;
+    int pad;           // shared-memory elements between the lines' regions (bank spread)
+    int threads;       // T W
+    int64_t ctas;
+    size_t smem;       // W (len + pad) elements
+};
+
 // Phase B on the d-dim groups {m + s' (n/p)} with every p_l <= 16, in one pass.
 // Tile = all p values for Mt consecutive m along the last axis.
 struct PhaseBFused {
@@ -142,6 +162,10 @@ cudaError_t launch_twiddle_table(void *dst, int64_t n, int is_double, cudaStream
 // out[i] *= mul[i] for i in [n] (used when phase B cannot fuse the multiply).
 cudaError_t launch_pointwise(void *out, const void *mul, int64_t n, int is_double, cudaStream_t st);
 cudaError_t launch_axis_pass(const AxisPass &a, int is_double, int dir, cudaStream_t st);
+cudaError_t prepare_line_pass(int dir);
+cudaError_t launch_line_pass(const LinePass &a, int dir, cudaStream_t st);
+// tw1 (len entries) then tw2 (len / 16 entries) of a line pass, generated in FP64 and rounded.
+cudaError_t launch_line_tables(void *dst, int len, cudaStream_t st);
 cudaError_t launch_phase_b_fused(const PhaseBFused &b, int is_double, int dir, cudaStream_t st);
 size_t axis_pass_smem_bytes(const AxisPass &a, int is_double);
 size_t phase_b_fused_smem_bytes(const PhaseBFused &b, int is_double);

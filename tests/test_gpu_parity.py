@@ -199,6 +199,54 @@ def test_long_lines(fftu, case, inverse):
     assert oracle.rel_l2(y, oracle.fftn(x.astype(np.complex128), inverse=inverse)) <= tolerance(dt, x.size)
 
 
+# ---- register-resident line passes (phase-A sub-FFTs of 256 ... 2048 points, complex64) ----------
+
+LINE_CASES = [
+    ((512, 512), (2, 2), np.complex64),          # len 256 on both axes: 16 lines per CTA
+    ((1024, 64), (2, 4), np.complex64),          # len 512 on a strided axis (8 inner positions per CTA)
+    ((64, 4096), (4, 4), np.complex64),          # len 1024 on the contiguous axis (4 classes per CTA)
+    ((8192, 8), (4, 2), np.complex64),           # len 2048 on a strided axis
+    ((4, 16384), (1, 16), np.complex64),         # len 1024, 16 classes of a 16384-point line
+    ((256, 8, 1024), (1, 2, 4), np.complex64),   # three passes: one strided-pass axis, one line pass
+    ((512, 4, 512), (2, 2, 2), np.complex64),    # three passes, two of them line passes
+]
+
+
+@pytest.mark.parametrize("case", LINE_CASES, ids=_id)
+@pytest.mark.parametrize("inverse", [False, True])
+@pytest.mark.parametrize("inplace", [False, True])
+def test_line_passes_match_oracle(fftu, case, inverse, inplace):
+    """Plans whose phase A runs sub-FFTs of 256 to 2048 points in registers (line_pass.cu), forward and
+    inverse, in and out of place (in place with an odd number of passes runs the first one in its
+    strided form), against the oracle; out of place leaves the input untouched."""
+    import torch
+    shape, p, dt = case
+    x = complex_uniform(4242 + len(shape), shape, dtype=dt)
+    t = torch.from_numpy(x).cuda()
+    with fftu.Plan(shape, p, dtype=t.dtype, inverse=inverse) as plan:
+        assert plan.info["workspace_bytes"] == x.size * x.itemsize  # phase A alternates with a workspace
+        out = t if inplace else torch.empty_like(t)
+        plan.exec(t, out)
+        torch.cuda.synchronize()
+        plan.check_device_status()
+        y = out.cpu().numpy()
+        if not inplace:
+            assert np.array_equal(t.cpu().numpy(), x)
+    ref = oracle.fftn(x.astype(np.complex128), inverse=inverse)
+    assert oracle.rel_l2(y, ref) <= tolerance(dt, x.size)
+
+
+@pytest.mark.parametrize("case", LINE_CASES[:4], ids=_id)
+def test_line_pass_phase_a_matches_model(fftu, case):
+    """Phase A alone through line passes = Supersteps 0 + 1 of the CPU model of Algorithm 2.3."""
+    shape, p, dt = case
+    x = complex_uniform(4343, shape, dtype=dt)
+    for inverse in (False, True):
+        wa, _ = run_gpu(fftu, x, p, inverse=inverse, phase=fftu.FFTU_PHASE_A)
+        w_ref = cm.phase_a(x.astype(np.complex128), p, inverse=inverse)
+        assert oracle.rel_l2(wa, w_ref) <= tolerance(dt, x.size)
+
+
 @pytest.mark.parametrize("p", [(128, 128), (8, 8)], ids=["p128", "p8"])
 def test_full_size_2d_16384(fftu, p):
     """The 2D 16384 x 16384 complex64 workload against the full FP64 oracle."""
