@@ -148,8 +148,9 @@ namespace {
 // Whole-line tiles aim at this many elements: 256 threads of 16 (complex64) or 8 (complex128)
 // values, so that two CTAs share an SM at the kernels' register count.
 constexpr int64_t kTileTargetC64 = 4096, kTileTargetC128 = 2048;
-// Threads per CTA of a line pass (T threads per line, kLineThreads / T lines).
-constexpr int kLineThreads = 256;
+// Threads per CTA of a line pass: T threads per line, min(16, kLineThreads / T) lines (16 lines of 256 points
+// take 256 threads; the 16 / W pad between the lines' shared regions needs W <= 16).
+constexpr int kLineThreads = 512;
 
 // Generic schedule: one strided pass per axis.  mode 0 = phase A, mode 1 = phase B.
 fftu_status make_axis_pass(const Plan &pl, int l, int mode, double scale, AxisPass &a) {
@@ -276,7 +277,7 @@ bool make_line_pass(const Plan &pl, int l, LinePass &a) {
     a.G = (int)pl.p[l];
     a.T = (int)(len / 16);
     a.contiguous = inner == 1;
-    int W = kLineThreads / a.T;  // lines per CTA
+    int W = std::min(16, kLineThreads / a.T);  // lines per CTA
     if (a.contiguous) {
         a.Wc = (int)std::min<int64_t>(W, a.G);
         a.Wo = (int)std::min<int64_t>(W / a.Wc, outer);
@@ -298,6 +299,7 @@ bool make_line_pass(const Plan &pl, int l, LinePass &a) {
     a.tw = pl.table(l);
     a.tw1 = pl.line_table(l);
     a.tw2 = static_cast<const char *>(pl.line_table(l)) + len * pl.esize;
+    a.twp = static_cast<const char *>(pl.line_table(l)) + (len + len / 16) * pl.esize;
     return true;
 }
 
@@ -708,7 +710,7 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
     for (int l = 0; l < d; ++l) {
         const int64_t len = line_len(n, pp, l, dtype, precision);
         pl->line_table_off[l] = len ? off : -1;
-        off += len ? len + len / 16 : 0;
+        off += len ? len + len / 16 + n[l] : 0;
     }
     pl->table_bytes = (size_t)off * pl->esize;
     e = cudaMalloc(&pl->tables, pl->table_bytes);
@@ -736,7 +738,7 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
                                  dtype == FFTU_C128, ps);
         if (e == cudaSuccess && pl->line_table_off[l] >= 0)
             e = launch_line_tables(static_cast<char *>(pl->tables) + pl->line_table_off[l] * pl->esize,
-                                   (int)(n[l] / pp[l]), ps);
+                                   (int)(n[l] / pp[l]), (int)n[l], ps);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
     cudaStreamDestroy(ps);

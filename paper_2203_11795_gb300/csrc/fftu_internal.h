@@ -60,6 +60,7 @@ struct LinePass {
     const void *tw;    // w_{nl}^e, e in [nl] (forward roots)
     const void *tw1;   // w_len^{(j k1) mod len} at k1 T + j, k1 in [16], j in [T]
     const void *tw2;   // w_T^{(j1 k2) mod T} at j1 16 + k2, j1 in [T / 16], k2 in [16]
+    const void *twp;   // w_{nl}^{(c k) mod nl} at c len + k (the axis twiddle in Put order)
     int64_t outer, inner;
     int nl, len, G, T;
     int contiguous;
@@ -164,8 +165,9 @@ cudaError_t launch_pointwise(void *out, const void *mul, int64_t n, int is_doubl
 cudaError_t launch_axis_pass(const AxisPass &a, int is_double, int dir, cudaStream_t st);
 cudaError_t prepare_line_pass(int dir);
 cudaError_t launch_line_pass(const LinePass &a, int dir, cudaStream_t st);
-// tw1 (len entries) then tw2 (len / 16 entries) of a line pass, generated in FP64 and rounded.
-cudaError_t launch_line_tables(void *dst, int len, cudaStream_t st);
+// tw1 (len entries), tw2 (len / 16 entries) and twp (nl entries) of a line pass, generated in FP64 and
+// rounded.
+cudaError_t launch_line_tables(void *dst, int len, int nl, cudaStream_t st);
 cudaError_t launch_phase_b_fused(const PhaseBFused &b, int is_double, int dir, cudaStream_t st);
 size_t axis_pass_smem_bytes(const AxisPass &a, int is_double);
 size_t phase_b_fused_smem_bytes(const PhaseBFused &b, int is_double);

@@ -83,7 +83,10 @@ __global__ void __launch_bounds__(kLineMaxThreads) line_pass_kernel(const __grid
         v[j2] = reg[k1 * T + (j ^ k1)];
     }
     dft16<DIR>(v);
-    const float2 *__restrict__ tw = static_cast<const float2 *>(a.tw);
+    // w_{nl}^{c k} of this line in Put order: entry c len + k (consecutive k of a class are adjacent, so a
+    // warp's twiddle loads are runs like its stores).  For T = 16 the plain table w_nl^e at e = c k is kept:
+    // it needs fewer registers there (four CTAs per SM; measured faster on 1024^3 at p = 4^3).
+    const float2 *__restrict__ twp = static_cast<const float2 *>(T == 16 ? a.tw : a.twp) + (T == 16 ? 0 : c * LEN + k1);
     float2 *__restrict__ dst = static_cast<float2 *>(a.dst) + out_off;
     const int64_t s_out = CONTIG ? 1 : a.inner;  // element stride of the output index k
     if constexpr (R3 == 1) {
@@ -91,7 +94,7 @@ __global__ void __launch_bounds__(kLineMaxThreads) line_pass_kernel(const __grid
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) {
             const int k = k1 + 16 * k2;
-            dst[(int64_t)k * s_out] = cmul(v[k2], dirw<DIR>(tw[c * k]));
+            dst[(int64_t)k * s_out] = cmul(v[k2], dirw<DIR>(twp[T == 16 ? c * k : 16 * k2]));
         }
     } else {
         const float2 *__restrict__ tw2 = static_cast<const float2 *>(a.tw2);
@@ -114,19 +117,23 @@ __global__ void __launch_bounds__(kLineMaxThreads) line_pass_kernel(const __grid
 #pragma unroll
             for (int k3 = 0; k3 < R3; ++k3) {
                 const int k = k1 + 16 * k2 + 256 * k3;
-                dst[(int64_t)k * s_out] = cmul(y[k3], dirw<DIR>(tw[c * k]));
+                dst[(int64_t)k * s_out] = cmul(y[k3], dirw<DIR>(twp[16 * k2 + 256 * k3]));
             }
         }
     }
 }
 
-// tw1[k1 T + j] = w_len^{(j k1) mod len}, then tw2[j1 16 + k2] = w_T^{(j1 k2) mod T}: forward roots in FP64,
-// rounded to FP32 (the inverse conjugates them in the kernel).
-__global__ void line_table_kernel(float2 *dst, int len) {
+// tw1[k1 T + j] = w_len^{(j k1) mod len}, then tw2[j1 16 + k2] = w_T^{(j1 k2) mod T}, then twp[c len + k] =
+// w_nl^{(c k) mod nl}: forward roots in FP64, rounded to FP32 (the inverse conjugates them in the kernel).
+__global__ void line_table_kernel(float2 *dst, int len, int nl) {
     const int T = len / 16;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len + T; e += gridDim.x * blockDim.x) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len + T + nl; e += gridDim.x * blockDim.x) {
         long long num, den;
-        if (e < len) {
+        if (e >= len + T) {  // Put order: entry c len + k holds w_nl^{c k}
+            const int f = e - len - T;
+            num = ((long long)(f / len) * (f % len)) % nl;
+            den = nl;
+        } else if (e < len) {
             const int k1 = e / T, j = e % T;
             num = ((long long)j * k1) % len;
             den = len;
@@ -192,9 +199,9 @@ cudaError_t launch_line_pass(const LinePass &a, int dir, cudaStream_t st) {
     return dir < 0 ? launch_dir<-1>(a, st) : launch_dir<1>(a, st);
 }
 
-cudaError_t launch_line_tables(void *dst, int len, cudaStream_t st) {
-    const int n = len + len / 16;
-    line_table_kernel<<<(n + 255) / 256, 256, 0, st>>>(static_cast<float2 *>(dst), len);
+cudaError_t launch_line_tables(void *dst, int len, int nl, cudaStream_t st) {
+    const int n = len + len / 16 + nl;
+    line_table_kernel<<<(n + 255) / 256, 256, 0, st>>>(static_cast<float2 *>(dst), len, nl);
     return cudaGetLastError();
 }
 
