@@ -13,8 +13,11 @@
 // from registers straight to its Put position, with two shared-memory exchanges in between.  The strided
 // pass instead keeps the whole tile in shared memory through every stage.
 //
-// Thread t of a CTA belongs to line t % W for all three stages, so that the lanes of a warp spread over
-// adjacent lines, whose elements are adjacent in memory (adjacent classes, or adjacent inner positions).
+// In stage 1 thread t takes line t % W, so that the lanes of a warp load adjacent lines, whose elements are
+// adjacent in memory (adjacent classes, or adjacent inner positions).  On a strided axis it keeps that line
+// (adjacent inner positions are adjacent in the output too); on the contiguous axis, where adjacent classes
+// land len apart in the output, stages 2 and 3 take line t / T instead, so that a warp stores runs of 16
+// consecutive outputs of one class.
 // Shared layout of a line's region (len elements, regions `pad` = 16 / W elements apart):
 //   exchange 1: (k1, j) at k1 T + (j ^ k1);   exchange 2: (k1, j1, k2) at (j1 16 + k2) 16 + k1.
 // A CPU count of the wavefronts of every access (tests/test_line_pass_maps.py) finds 2 per 32 lanes, the
@@ -27,26 +30,29 @@
 namespace fftu {
 namespace {
 
-constexpr int kLineMaxThreads = 512;
+constexpr int kLineMaxThreads = 512;  // two CTAs of 512 (or four of 256) threads per SM: at most 64 registers
 
 template <int T, int DIR, bool CONTIG>
-__global__ void __launch_bounds__(kLineMaxThreads) line_pass_kernel(const __grid_constant__ LinePass a) {
+__global__ void __launch_bounds__(kLineMaxThreads, 2) line_pass_kernel(const __grid_constant__ LinePass a) {
     constexpr int LEN = 16 * T;
     constexpr int R3 = T / 16;
     extern __shared__ __align__(16) float2 line_sm[];
     const int t = threadIdx.x;
     const int w = t & (a.W - 1);  // line of this thread within the CTA
     const int q = t >> a.lg_W;    // role within the line, q in [T]
+    const int w2 = CONTIG ? t / T : w;  // line of this thread in stages 2 and 3
+    const int q2 = CONTIG ? t % T : q;
     const int64_t b = blockIdx.x;
     int64_t in_off, out_off;
-    int c;  // residue class of the line
+    int c;  // residue class of the stage-2/3 line
     if constexpr (CONTIG) {
         const int lg_cgroups = __ffs(a.G) - 1 - a.lg_Wc;
         const int64_t cg = b & ((1ll << lg_cgroups) - 1), og = b >> lg_cgroups;
         const int64_t o = og * a.Wo + (w >> a.lg_Wc);
-        c = (int)((cg << a.lg_Wc) + (w & (a.Wc - 1)));
-        in_off = o * a.nl + c;
-        out_off = o * a.nl + (int64_t)c * LEN;
+        in_off = o * a.nl + (cg << a.lg_Wc) + (w & (a.Wc - 1));
+        const int64_t o2 = og * a.Wo + (w2 >> a.lg_Wc);
+        c = (int)((cg << a.lg_Wc) + (w2 & (a.Wc - 1)));
+        out_off = o2 * a.nl + (int64_t)c * LEN;
     } else {
         const int64_t vgroups = a.inner >> a.lg_W;
         const int64_t vg = b % vgroups, rest = b / vgroups;
@@ -76,7 +82,8 @@ __global__ void __launch_bounds__(kLineMaxThreads) line_pass_kernel(const __grid
     __syncthreads();
 
     // stage 2: thread (k1, j1): F_16 over j2 of the values j = j1 + R3 j2
-    const int k1 = q & 15, j1 = q >> 4;
+    reg = line_sm + w2 * (LEN + a.pad);
+    const int k1 = q2 & 15, j1 = q2 >> 4;
 #pragma unroll
     for (int j2 = 0; j2 < 16; ++j2) {
         const int j = j1 + R3 * j2;

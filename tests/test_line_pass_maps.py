@@ -5,6 +5,8 @@ twiddle of Sec. 2.2 and the Put position s len + k of Superstep 1) with len = 16
 radix split of Sec. 2.1.1 (eq. radix).  This file restates its thread roles and shared-memory maps in
 numpy and checks, for every T and CTA width W the planner can choose:
 
+* on the contiguous axis, where stages 2 and 3 take line-major roles, a warp's Put stores are runs of 16
+  consecutive outputs of one line;
 * the data carried through the maps for one CTA equals the length-len DFT of every line times
   w_{n_l}^{k c} (numpy's FFT as the DFT primitive), both directions;
 * every shared-memory access stays inside the CTA's buffer and each exchange's store map is a
@@ -53,10 +55,11 @@ def wavefronts(byte_addrs):
 
 
 class Mirror:
-    """One CTA of W lines: thread t takes line t % W and role q = t / W in every stage."""
+    """One CTA of W lines.  Stage 1: thread t takes line t % W and role q = t / W.  Stages 2 and 3: the same
+    on a strided axis; on the contiguous axis line t / T and role t % T."""
 
-    def __init__(self, T, W):
-        self.T, self.W = T, W
+    def __init__(self, T, W, contig=False):
+        self.T, self.W, self.contig = T, W, contig
         self.LEN = 16 * T
         self.R3 = T // 16
         self.P = pad_of(W)
@@ -65,6 +68,9 @@ class Mirror:
 
     def region(self, w):
         return w * (self.LEN + self.P)
+
+    def role2(self, t):
+        return (t // self.T, t % self.T) if self.contig else (t % self.W, t // self.W)
 
     def ex1(self, k1, j):
         return k1 * self.T + (j ^ k1)
@@ -79,17 +85,16 @@ class Mirror:
         acc = []
         for k1 in range(16):  # stage-1 store
             acc.append(("ex1_store", [self.region(t % W) + self.ex1(k1, t // W) for t in th]))
+        r2 = [self.role2(t) for t in th]
         for j2 in range(16):  # stage-2 load
-            acc.append(("ex1_load", [self.region(t % W) + self.ex1((t // W) & 15, ((t // W) >> 4) + R3 * j2)
-                                     for t in th]))
+            acc.append(("ex1_load", [self.region(w) + self.ex1(q & 15, (q >> 4) + R3 * j2) for w, q in r2]))
         if R3 > 1:
             for k2 in range(16):  # stage-2 store
-                acc.append(("ex2_store", [self.region(t % W) + self.ex2((t // W) & 15, (t // W) >> 4, k2)
-                                          for t in th]))
+                acc.append(("ex2_store", [self.region(w) + self.ex2(q & 15, q >> 4, k2) for w, q in r2]))
             for i in range(16 // R3):  # stage-3 loads
                 for jj in range(R3):
-                    acc.append(("ex2_load", [self.region(t % W) +
-                                             self.ex2((t // W) & 15, jj, ((t // W) >> 4) + R3 * i) for t in th]))
+                    acc.append(("ex2_load", [self.region(w) + self.ex2(q & 15, jj, (q >> 4) + R3 * i)
+                                             for w, q in r2]))
         return acc
 
     def run(self, x, c, nl, sign):
@@ -105,26 +110,27 @@ class Mirror:
             for k1 in range(16):
                 sm[self.region(w) + self.ex1(k1, j)] = v[k1]
         for t in range(self.threads):
-            w, q = t % W, t // W
+            w, q = self.role2(t)
             k1, j1 = q & 15, q >> 4
             v = np.array([sm[self.region(w) + self.ex1(k1, j1 + R3 * j2)] for j2 in range(16)])
             regs[t] = dft(v, sign)
         if R3 == 1:
             for t in range(self.threads):
-                w, k1 = t % W, (t // W) & 15
+                w, q = self.role2(t)
+                k1 = q & 15
                 for k2 in range(16):
                     k = k1 + 16 * k2
                     out[w, k] = regs[t][k2] * root(nl, c[w] * k, sign)
             return out
         sm[:] = np.nan
         for t in range(self.threads):
-            w, q = t % W, t // W
+            w, q = self.role2(t)
             k1, j1 = q & 15, q >> 4
             v = regs[t] * root(T, j1 * np.arange(16), sign)
             for k2 in range(16):
                 sm[self.region(w) + self.ex2(k1, j1, k2)] = v[k2]
         for t in range(self.threads):
-            w, q = t % W, t // W
+            w, q = self.role2(t)
             k1, h = q & 15, q >> 4
             for i in range(16 // R3):
                 k2 = h + R3 * i
@@ -136,8 +142,9 @@ class Mirror:
 
 
 @pytest.mark.parametrize("T,W", line_configs(), ids=lambda v: str(v))
-def test_shared_maps_in_bounds_bijective_and_conflict_free(T, W):
-    m = Mirror(T, W)
+@pytest.mark.parametrize("contig", [False, True], ids=["strided", "contiguous"])
+def test_shared_maps_in_bounds_bijective_and_conflict_free(T, W, contig):
+    m = Mirror(T, W, contig)
     acc = m.accesses()
     for name, idx in acc:
         idx = np.asarray(idx)
@@ -162,8 +169,9 @@ def test_shared_maps_in_bounds_bijective_and_conflict_free(T, W):
 
 @pytest.mark.parametrize("T,W", [(16, 16), (32, 8), (64, 4), (128, 2), (64, 1), (128, 4)], ids=lambda v: str(v))
 @pytest.mark.parametrize("sign", [-1, 1])
-def test_line_data_equals_dft_twiddle(T, W, sign):
-    m = Mirror(T, W)
+@pytest.mark.parametrize("contig", [False, True], ids=["strided", "contiguous"])
+def test_line_data_equals_dft_twiddle(T, W, sign, contig):
+    m = Mirror(T, W, contig)
     G = 4
     nl = m.LEN * G
     u = uniform_pm1(1000 + T + W, np.arange(2 * W * m.LEN, dtype=np.uint64))
@@ -226,3 +234,20 @@ def test_cta_decode_covers_input_and_put_positions(case):
             np.add.at(seen_in, idx_in, 1)
             np.add.at(seen_out, idx_out, 1)
     assert np.all(seen_in == 1) and np.all(seen_out == 1)
+
+
+@pytest.mark.parametrize("T,W", line_configs(), ids=lambda v: str(v))
+def test_contiguous_put_stores_are_runs(T, W):
+    """Stage-3 (or, for T = 16, stage-2) stores of one warp on the contiguous axis: runs of at least 16
+    consecutive k of one line."""
+    m = Mirror(T, W, contig=True)
+    for w0 in range(0, m.threads, 32):
+        roles = [m.role2(t) for t in range(w0, min(w0 + 32, m.threads))]
+        for k2 in range(16 if m.R3 == 1 else 1):
+            by_line = defaultdict(list)
+            for w, q in roles:
+                by_line[w].append((q & 15) + 16 * (k2 if m.R3 == 1 else (q >> 4)))
+            for ks in by_line.values():
+                ks = sorted(ks)
+                runs = sum(1 for i, k in enumerate(ks) if i == 0 or k != ks[i - 1] + 1)
+                assert len(ks) % 16 == 0 and runs <= len(ks) // 16  # every run at least 16 long
