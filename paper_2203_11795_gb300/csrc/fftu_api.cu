@@ -148,8 +148,9 @@ namespace {
 // Whole-line tiles aim at this many elements: 256 threads of 16 (complex64) or 8 (complex128)
 // values, so that two CTAs share an SM at the kernels' register count.
 constexpr int64_t kTileTargetC64 = 4096, kTileTargetC128 = 2048;
-// Threads per CTA of a line pass: T threads per line, min(16, kLineThreads / T) lines (16 lines of 256 points
-// take 256 threads; the 16 / W pad between the lines' shared regions needs W <= 16).
+// Threads per CTA of a line pass: T threads per line, min(16, max(8, kLineThreads / T)) lines (16 lines of
+// 256 points take 256 threads, 8 lines of 2048 points 1024; the 16 / W pad between the lines' shared regions
+// needs W <= 16).
 constexpr int kLineThreads = 512;
 
 // Generic schedule: one strided pass per axis.  mode 0 = phase A, mode 1 = phase B.
@@ -277,7 +278,7 @@ bool make_line_pass(const Plan &pl, int l, LinePass &a) {
     a.G = (int)pl.p[l];
     a.T = (int)(len / 16);
     a.contiguous = inner == 1;
-    int W = std::min(16, kLineThreads / a.T);  // lines per CTA
+    int W = std::min(16, std::max(8, kLineThreads / a.T));  // lines per CTA
     if (a.contiguous) {
         a.Wc = (int)std::min<int64_t>(W, a.G);
         a.Wo = (int)std::min<int64_t>(W / a.Wc, outer);
@@ -295,7 +296,9 @@ bool make_line_pass(const Plan &pl, int l, LinePass &a) {
     a.pad = W >= 2 ? 16 / W : 0;
     a.threads = a.T * W;
     a.smem = (size_t)W * (size_t)(len + a.pad) * pl.esize;
-    if (a.threads < 32 || a.threads > 512 || a.smem > (size_t)kMaxDynSmem || a.ctas > 0x7fffffffll) return false;
+    if (a.threads < 32 || a.threads > (a.T == 128 ? 1024 : 512) || a.smem > (size_t)kMaxDynSmem ||
+        a.ctas > 0x7fffffffll)
+        return false;
     a.tw = pl.table(l);
     a.tw1 = pl.line_table(l);
     a.tw2 = static_cast<const char *>(pl.line_table(l)) + len * pl.esize;

@@ -30,10 +30,14 @@
 namespace fftu {
 namespace {
 
-constexpr int kLineMaxThreads = 512;  // two CTAs of 512 (or four of 256) threads per SM: at most 64 registers
+// At most 64 registers: two CTAs of 512 threads (or four of 256) per SM; 2048-point lines take eight lines
+// per CTA, 1024 threads (one CTA per SM; measured faster than four lines per CTA).
+constexpr int kLineMaxThreads = 1024;
+template <int T> constexpr int line_max_threads() { return T == 128 ? 1024 : 512; }
 
 template <int T, int DIR, bool CONTIG>
-__global__ void __launch_bounds__(kLineMaxThreads, 2) line_pass_kernel(const __grid_constant__ LinePass a) {
+__global__ void __launch_bounds__(line_max_threads<T>(), line_max_threads<T>() == 1024 ? 1 : 2)
+    line_pass_kernel(const __grid_constant__ LinePass a) {
     constexpr int LEN = 16 * T;
     constexpr int R3 = T / 16;
     extern __shared__ __align__(16) float2 line_sm[];
@@ -201,6 +205,7 @@ cudaError_t prepare_line_pass(int dir) { return dir < 0 ? prepare_dir<-1>() : pr
 
 cudaError_t launch_line_pass(const LinePass &a, int dir, cudaStream_t st) {
     if (a.ctas < 1 || a.threads < 32 || a.threads > kLineMaxThreads || a.threads != a.T * a.W ||
+        (a.T != 128 && a.threads > 512) ||
         a.ctas > 0x7fffffffll || a.smem > (size_t)kMaxDynSmem)
         return cudaErrorInvalidValue;
     return dir < 0 ? launch_dir<-1>(a, st) : launch_dir<1>(a, st);

@@ -32,7 +32,7 @@ def line_configs():
     out = []
     for T in (16, 32, 64, 128):
         for W in (1, 2, 4, 8, 16):
-            if 32 <= T * W <= 512:
+            if 32 <= T * W <= (1024 if T == 128 else 512):
                 out.append((T, W))
     return out
 
