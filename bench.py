@@ -1048,6 +1048,7 @@ def run_batch(args):
 SECONDARY = [
     ("1024^3_c64_p16x16x8", "run", dict(shape="1024,1024,1024", p="16,16,8", steps=5, warmup=3, inputs="device")),
     ("1024^3_c64_p8x8x8", "run", dict(shape="1024,1024,1024", p="8,8,8", steps=5, warmup=3, inputs="device")),
+    ("1024^3_c64_p4x4x4", "run", dict(shape="1024,1024,1024", p="4,4,4", steps=5, warmup=3, inputs="device")),
     ("512^3_c64_split_bf16", "run", dict(precision="bf16", steps=10, warmup=3, inputs="device")),
     ("512^3_c64_split_fp16", "run", dict(precision="fp16", steps=10, warmup=3, inputs="device")),
     ("512^3_c64_split_bf16_loguniform", "run", dict(precision="bf16", steps=10, warmup=3,

@@ -81,14 +81,18 @@ int radix_plan_tc(int len, int *radix) {
     return n;
 }
 
-enum StepKind { STEP_AXIS = 1, STEP_PHASE_B_FUSED = 2, STEP_PHASE_B3 = 3, STEP_PHASE_A3 = 4, STEP_LINE = 5 };
+enum StepKind {
+    STEP_AXIS = 1, STEP_PHASE_B_FUSED = 2, STEP_PHASE_B3 = 3, STEP_PHASE_A3 = 4, STEP_LINE = 5, STEP_PAIR = 6
+};
 
 struct Step {
     int kind;
-    AxisPass axis;  // STEP_LINE keeps the strided-pass form of the same axis (in place; batching)
+    AxisPass axis;   // STEP_LINE and STEP_PAIR keep the strided-pass form of the same axis (in place; batching)
+    AxisPass axis2;  // STEP_PAIR: the strided-pass form of the pair's first axis (run after `axis`)
     PhaseBFused pb;
     Phase3Launch a3;
     LinePass line;
+    PairPass pair;
 };
 
 // Residue units up to this size run phase A as one persistent kernel through a
@@ -306,15 +310,71 @@ bool make_line_pass(const Plan &pl, int l, LinePass &a) {
     return true;
 }
 
+// Axes a = b - 1 and b in one register-resident pass (pair_pass.cu), when it serves them.
+bool make_pair_pass(const Plan &pl, int b, PairPass &a) {
+    std::memset(&a, 0, sizeof(a));
+    if (b < 1 || pl.dtype != FFTU_C64 || pl.precision != FFTU_PREC_NATIVE) return false;
+    const int ax = b - 1;
+    if (pl.p[ax] < 2 || pl.p[b] < 2) return false;
+    const int64_t L = pl.n[b] / pl.p[b];
+    if (pl.n[ax] / pl.p[ax] != L || (L != 8 && L != 16) || pl.p[ax] * pl.p[b] < 16) return false;
+    int64_t outer = 1, inner = 1;
+    for (int k = 0; k < ax; ++k) outer *= pl.n[k];
+    for (int k = b + 1; k < pl.d; ++k) inner *= pl.n[k];
+    const int64_t per_item = pl.p[ax] * pl.p[b] * L;  // threads per item
+    if (per_item > 1024) return false;
+    a.outer = outer;
+    a.inner = inner;
+    a.na = (int)pl.n[ax];
+    a.nb = (int)pl.n[b];
+    a.pa = (int)pl.p[ax];
+    a.pb = (int)pl.p[b];
+    a.L = (int)L;
+    a.lg_pa = ilog2(a.pa);
+    a.lg_pb = ilog2(a.pb);
+    a.contiguous = inner == 1;
+    int64_t W;
+    if (a.contiguous) {  // adjacent planes: up to 512 threads
+        W = std::max<int64_t>(1, 512 / per_item);
+        W = std::min(W, outer);
+        a.ctas = outer / W;
+        a.pad = 0;
+    } else {  // adjacent inner positions: runs of W elements, at least 4
+        W = std::min<int64_t>(std::min<int64_t>(16, 1024 / per_item), inner);
+        if (W < 4) return false;
+        a.ctas = outer * (inner / W);
+        a.pad = (int)(16 / W);
+    }
+    a.W = (int)W;
+    a.lg_W = ilog2(a.W);
+    a.threads = (int)(W * per_item);
+    a.smem = (size_t)W * (size_t)(per_item * L + a.pad) * pl.esize;
+    if (a.smem > (size_t)kMaxDynSmem || a.ctas > 0x7fffffffll) return false;
+    a.twa = pl.table(ax);
+    a.twb = pl.table(b);
+    return true;
+}
+
 fftu_status build_generic_phase_a(Plan &pl, std::vector<Step> &out, bool allow_line) {
-    // Contiguous axis first (reads the caller's array in long runs).
+    // Contiguous axis first (reads the caller's array in long runs).  Out of place, two adjacent axes
+    // with short sub-FFTs go through HBM once (pair pass); long sub-FFTs take the line pass.
     for (int l = pl.d - 1; l >= 0; --l) {
         if (pl.n[l] == 1) continue;
         Step s;
         std::memset(&s.line, 0, sizeof(s.line));
+        std::memset(&s.pair, 0, sizeof(s.pair));
+        std::memset(&s.axis2, 0, sizeof(s.axis2));
         s.kind = STEP_AXIS;
         fftu_status st = make_axis_pass(pl, l, 0, 1.0, s.axis);
         if (st != FFTU_OK) return st;
+        if (allow_line && l >= 1 && pl.n[l - 1] > 1 && make_pair_pass(pl, l, s.pair)) {
+            st = make_axis_pass(pl, l - 1, 0, 1.0, s.axis2);
+            if (st != FFTU_OK) return st;
+            s.kind = STEP_PAIR;
+            out.push_back(s);
+            --l;
+            continue;
+        }
         if (allow_line && make_line_pass(pl, l, s.line)) s.kind = STEP_LINE;
         out.push_back(s);
     }
@@ -385,8 +445,9 @@ fftu_status build_schedule(Plan &pl, int sched) {
         // a pass over part of the classes of a line, or a line pass, is not in place: alternate with a
         // workspace
         for (const Step &s : pl.phase_a) {
-            if (s.axis.Gt < s.axis.G) pl.axis_pingpong = true;
-            if (s.kind == STEP_LINE || s.axis.Gt < s.axis.G) pl.generic_pingpong = true;
+            const bool long_line = s.axis.Gt < s.axis.G || (s.kind == STEP_PAIR && s.axis2.Gt < s.axis2.G);
+            if (long_line) pl.axis_pingpong = true;
+            if (s.kind == STEP_LINE || s.kind == STEP_PAIR || long_line) pl.generic_pingpong = true;
         }
         if (pl.generic_pingpong) pl.ws_natural = (size_t)pl.N * pl.esize;
     }
@@ -468,8 +529,8 @@ fftu_status run_steps(Plan *pl, const std::vector<Step> &steps, const void *firs
             a.src = src;
             a.dst = dst;
             e = launch_axis_pass(a, is_double, pl->dir, st);
-        } else if (s.kind == STEP_LINE) {
-            record_error("internal: a line pass outside the alternating phase-A schedule");
+        } else if (s.kind == STEP_LINE || s.kind == STEP_PAIR) {
+            record_error("internal: a line or pair pass outside the alternating phase-A schedule");
             return FFTU_ERR_INTERNAL;
         } else if (s.kind == STEP_PHASE_A3) {
             Phase3Launch l = s.a3;
@@ -531,6 +592,10 @@ fftu_status plan_view(fftu_handle h, PlanView *v) {
         sv.is_axis = true;
         sv.axis = s.axis;
         v->a_passes.push_back(sv);
+        if (s.kind == STEP_PAIR) {  // the pair's first axis, in its strided-pass form
+            sv.axis = s.axis2;
+            v->a_passes.push_back(sv);
+        }
     }
     const double scale = pl.dir == FFTU_INVERSE ? 1.0 / (double)pl.N : 1.0;
     for (const Step &s : pl.phase_b) {
@@ -753,6 +818,7 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
     if (e == cudaSuccess) e = prepare_phase_b_fused(dtype == FFTU_C128, dir);
     if (e == cudaSuccess) e = prepare_phase_b3(dtype == FFTU_C128, dir);
     if (e == cudaSuccess && dtype == FFTU_C64) e = prepare_line_pass(dir);
+    if (e == cudaSuccess && dtype == FFTU_C64) e = prepare_pair_pass(dir);
     if (e != cudaSuccess) {
         free_plan(pl);
         return cuda_fail(e, "kernel attributes");
@@ -810,7 +876,7 @@ fftu_status exec_natural(Plan *pl, fftu_phase phase, const void *in, void *out, 
         for (int k = 1; k <= np; ++k) {
             const Step &s = pl->phase_a[k - 1];
             void *dst = ((np - k) % 2 == 0) ? out : pl->workspace;
-            const bool whole_lines = s.axis.Gt == s.axis.G;
+            const bool whole_lines = s.axis.Gt == s.axis.G && (s.kind != STEP_PAIR || s.axis2.Gt == s.axis2.G);
             if (dst == src && !(k == 1 && whole_lines && src == out)) {
                 set_err("in-place transform with a long-line axis needs in != out");
                 return FFTU_ERR_UNSUPPORTED;
@@ -821,6 +887,17 @@ fftu_status exec_natural(Plan *pl, fftu_phase phase, const void *in, void *out, 
                 a.src = src;
                 a.dst = out;
                 e = launch_axis_pass(a, pl->dtype == FFTU_C128, pl->dir, st);
+                if (e == cudaSuccess && s.kind == STEP_PAIR) {
+                    a = s.axis2;
+                    a.src = out;
+                    a.dst = out;
+                    e = launch_axis_pass(a, pl->dtype == FFTU_C128, pl->dir, st);
+                }
+            } else if (s.kind == STEP_PAIR) {
+                PairPass a = s.pair;
+                a.src = src;
+                a.dst = dst;
+                e = launch_pair_pass(a, pl->dir, st);
             } else if (s.kind == STEP_LINE) {
                 LinePass a = s.line;
                 a.src = src;

@@ -71,6 +71,25 @@ struct LinePass {
     size_t smem;       // W (len + pad) elements
 };
 
+// Phase A of two adjacent axes a, b = a + 1 in one pass (complex64; see pair_pass.cu), for equal sub-FFT
+// lengths L = n_a / p_a = n_b / p_b in {8, 16} and p_a p_b >= 16.  Same result as two AxisPass of mode 0
+// (axis b, then axis a), never in place.  The array is viewed as [outer][n_a][n_b][inner]; a CTA runs W
+// planes (inner == 1) or W adjacent inner positions, p_a p_b L threads per item.
+struct PairPass {
+    const void *src;
+    void *dst;
+    const void *twa, *twb;  // w_{n_a}^e and w_{n_b}^e (forward roots)
+    int64_t outer, inner;
+    int na, nb, pa, pb, L;
+    int lg_pa, lg_pb;
+    int contiguous;         // inner == 1
+    int W, lg_W;
+    int pad;                // shared-memory elements between the items' regions (bank spread)
+    int threads;            // W p_a p_b L
+    int64_t ctas;
+    size_t smem;            // W (p_a p_b L^2 + pad) elements
+};
+
 // Phase B on the d-dim groups {m + s' (n/p)} with every p_l <= 16, in one pass.
 // Tile = all p values for Mt consecutive m along the last axis.
 struct PhaseBFused {
@@ -164,6 +183,8 @@ cudaError_t launch_twiddle_table(void *dst, int64_t n, int is_double, cudaStream
 cudaError_t launch_pointwise(void *out, const void *mul, int64_t n, int is_double, cudaStream_t st);
 cudaError_t launch_axis_pass(const AxisPass &a, int is_double, int dir, cudaStream_t st);
 cudaError_t prepare_line_pass(int dir);
+cudaError_t prepare_pair_pass(int dir);
+cudaError_t launch_pair_pass(const PairPass &a, int dir, cudaStream_t st);
 cudaError_t launch_line_pass(const LinePass &a, int dir, cudaStream_t st);
 // tw1 (len entries), tw2 (len / 16 entries) and twp (nl entries) of a line pass, generated in FP64 and
 // rounded.

@@ -262,8 +262,13 @@ bool make_room(fftu_server_st *S, size_t need, const KeyState *keep) {
 // The resident plan of a key (batched requests); nullptr if it does not fit now or fails.
 fftu_status ensure_plan(fftu_server_st *S, KeyState *ks) {
     if (ks->plan) return FFTU_OK;
+    // the batch kernel runs the plan's in-place passes and never its workspace: the plan allocates none
+    fftu_options opts;
+    std::memset(&opts, 0, sizeof(opts));
+    opts.workspace_mode = FFTU_WORKSPACE_CALLER;
     fftu_handle h = nullptr;
-    fftu_status st = fftu_plan(ks->key.d, ks->key.n, nullptr, (fftu_dtype)ks->key.dtype, (fftu_dir)ks->key.dir, &h);
+    fftu_status st = fftu_plan_ex(ks->key.d, ks->key.n, nullptr, (fftu_dtype)ks->key.dtype, (fftu_dir)ks->key.dir,
+                                  &opts, &h);
     if (st != FFTU_OK) return st;
     const size_t b = plan_device_bytes(h);
     if (S->used + b > (size_t)S->cfg.device_bytes && !make_room(S, b, ks)) {

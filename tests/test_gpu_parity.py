@@ -247,6 +247,53 @@ def test_line_pass_phase_a_matches_model(fftu, case):
         assert oracle.rel_l2(wa, w_ref) <= tolerance(dt, x.size)
 
 
+# ---- two-axis pair passes (phase A of two adjacent axes with 8- or 16-point sub-FFTs, complex64) -------
+
+PAIR_CASES = [
+    ((64, 32, 32), (4, 4, 4), np.complex64),          # contiguous pair (4 planes per CTA), then one axis
+    ((32, 32, 16), (4, 4, 2), np.complex64),          # one axis, then a strided pair (8 inner positions)
+    ((64, 64), (8, 8), np.complex64),                 # one pair step only (p_a p_b = 64, 512 threads)
+    ((2, 64, 64, 4), (1, 4, 4, 2), np.complex64),     # 16-point pair in the middle, three steps
+    ((2, 32, 32, 32, 32), (1, 4, 4, 4, 4), np.complex64),  # two pairs and one axis (the 32^5 layout)
+    ((32, 32, 32, 32), (4, 4, 4, 4), np.complex64),   # two pairs
+]
+
+
+@pytest.mark.parametrize("case", PAIR_CASES, ids=_id)
+@pytest.mark.parametrize("inverse", [False, True])
+@pytest.mark.parametrize("inplace", [False, True])
+def test_pair_passes_match_oracle(fftu, case, inverse, inplace):
+    """Plans whose phase A runs two adjacent axes per pass (pair_pass.cu), forward and inverse, in and out
+    of place (in place with an odd number of steps runs the first one as two strided passes), against the
+    oracle; out of place leaves the input untouched."""
+    import torch
+    shape, p, dt = case
+    x = complex_uniform(5151 + len(shape), shape, dtype=dt)
+    t = torch.from_numpy(x).cuda()
+    with fftu.Plan(shape, p, dtype=t.dtype, inverse=inverse) as plan:
+        assert plan.info["workspace_bytes"] == x.size * x.itemsize  # phase A alternates with a workspace
+        out = t if inplace else torch.empty_like(t)
+        plan.exec(t, out)
+        torch.cuda.synchronize()
+        plan.check_device_status()
+        y = out.cpu().numpy()
+        if not inplace:
+            assert np.array_equal(t.cpu().numpy(), x)
+    ref = oracle.fftn(x.astype(np.complex128), inverse=inverse)
+    assert oracle.rel_l2(y, ref) <= tolerance(dt, x.size)
+
+
+@pytest.mark.parametrize("case", PAIR_CASES[:4], ids=_id)
+def test_pair_pass_phase_a_matches_model(fftu, case):
+    """Phase A alone through pair passes = Supersteps 0 + 1 of the CPU model of Algorithm 2.3."""
+    shape, p, dt = case
+    x = complex_uniform(5252, shape, dtype=dt)
+    for inverse in (False, True):
+        wa, _ = run_gpu(fftu, x, p, inverse=inverse, phase=fftu.FFTU_PHASE_A)
+        w_ref = cm.phase_a(x.astype(np.complex128), p, inverse=inverse)
+        assert oracle.rel_l2(wa, w_ref) <= tolerance(dt, x.size)
+
+
 @pytest.mark.parametrize("p", [(128, 128), (8, 8)], ids=["p128", "p8"])
 def test_full_size_2d_16384(fftu, p):
     """The 2D 16384 x 16384 complex64 workload against the full FP64 oracle."""
