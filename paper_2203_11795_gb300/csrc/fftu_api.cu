@@ -82,17 +82,28 @@ int radix_plan_tc(int len, int *radix) {
 }
 
 enum StepKind {
-    STEP_AXIS = 1, STEP_PHASE_B_FUSED = 2, STEP_PHASE_B3 = 3, STEP_PHASE_A3 = 4, STEP_LINE = 5, STEP_PAIR = 6
+    STEP_AXIS = 1, STEP_PHASE_B_FUSED = 2, STEP_PHASE_B3 = 3, STEP_PHASE_A3 = 4, STEP_LINE = 5, STEP_PAIR = 6,
+    STEP_TRIPLE = 7
 };
 
 struct Step {
     int kind;
     AxisPass axis;   // STEP_LINE and STEP_PAIR keep the strided-pass form of the same axis (in place; batching)
-    AxisPass axis2;  // STEP_PAIR: the strided-pass form of the pair's first axis (run after `axis`)
+    AxisPass axis2;  // STEP_PAIR / STEP_TRIPLE: the strided-pass form of the next axis down (run after `axis`)
+    AxisPass axis3;  // STEP_TRIPLE: the strided-pass form of the third axis (run after `axis2`)
     PhaseBFused pb;
     Phase3Launch a3;
     LinePass line;
     PairPass pair;
+    TriplePass triple;
+
+    int passes() const { return kind == STEP_TRIPLE ? 3 : kind == STEP_PAIR ? 2 : 1; }
+    const AxisPass &strided(int i) const { return i == 0 ? axis : i == 1 ? axis2 : axis3; }
+    bool whole_lines() const {
+        for (int i = 0; i < passes(); ++i)
+            if (strided(i).Gt < strided(i).G) return false;
+        return true;
+    }
 };
 
 // Residue units up to this size run phase A as one persistent kernel through a
@@ -355,6 +366,34 @@ bool make_pair_pass(const Plan &pl, int b, PairPass &a) {
     return true;
 }
 
+// The last three axes in one register-resident pass (triple_pass.cu), when it serves them.
+bool make_triple_pass(const Plan &pl, TriplePass &a) {
+    std::memset(&a, 0, sizeof(a));
+    const int c = pl.d - 1, b = c - 1, ax = c - 2;
+    if (pl.d < 3 || pl.dtype != FFTU_C64 || pl.precision != FFTU_PREC_NATIVE) return false;
+    for (int l = ax; l <= c; ++l)
+        if (pl.p[l] < 2 || pl.n[l] != 8 * pl.p[l]) return false;
+    if (pl.p[b] * pl.p[c] != 16) return false;
+    int64_t outer = 1;
+    for (int k = 0; k < ax; ++k) outer *= pl.n[k];
+    a.outer = outer;
+    a.na = (int)pl.n[ax];
+    a.nb = (int)pl.n[b];
+    a.nc = (int)pl.n[c];
+    a.pa = (int)pl.p[ax];
+    a.pb = (int)pl.p[b];
+    a.pc = (int)pl.p[c];
+    a.lg_pa = ilog2(a.pa);
+    a.lg_pc = ilog2(a.pc);
+    a.ctas = outer * a.pa;
+    a.smem = (size_t)8192 * pl.esize;
+    if (a.ctas > 0x7fffffffll) return false;
+    a.twa = pl.table(ax);
+    a.twb = pl.table(b);
+    a.twc = pl.table(c);
+    return true;
+}
+
 fftu_status build_generic_phase_a(Plan &pl, std::vector<Step> &out, bool allow_line) {
     // Contiguous axis first (reads the caller's array in long runs).  Out of place, two adjacent axes
     // with short sub-FFTs go through HBM once (pair pass); long sub-FFTs take the line pass.
@@ -363,10 +402,21 @@ fftu_status build_generic_phase_a(Plan &pl, std::vector<Step> &out, bool allow_l
         Step s;
         std::memset(&s.line, 0, sizeof(s.line));
         std::memset(&s.pair, 0, sizeof(s.pair));
+        std::memset(&s.triple, 0, sizeof(s.triple));
         std::memset(&s.axis2, 0, sizeof(s.axis2));
+        std::memset(&s.axis3, 0, sizeof(s.axis3));
         s.kind = STEP_AXIS;
         fftu_status st = make_axis_pass(pl, l, 0, 1.0, s.axis);
         if (st != FFTU_OK) return st;
+        if (allow_line && l == pl.d - 1 && make_triple_pass(pl, s.triple)) {
+            st = make_axis_pass(pl, l - 1, 0, 1.0, s.axis2);
+            if (st == FFTU_OK) st = make_axis_pass(pl, l - 2, 0, 1.0, s.axis3);
+            if (st != FFTU_OK) return st;
+            s.kind = STEP_TRIPLE;
+            out.push_back(s);
+            l -= 2;
+            continue;
+        }
         if (allow_line && l >= 1 && pl.n[l - 1] > 1 && make_pair_pass(pl, l, s.pair)) {
             st = make_axis_pass(pl, l - 1, 0, 1.0, s.axis2);
             if (st != FFTU_OK) return st;
@@ -445,9 +495,9 @@ fftu_status build_schedule(Plan &pl, int sched) {
         // a pass over part of the classes of a line, or a line pass, is not in place: alternate with a
         // workspace
         for (const Step &s : pl.phase_a) {
-            const bool long_line = s.axis.Gt < s.axis.G || (s.kind == STEP_PAIR && s.axis2.Gt < s.axis2.G);
+            const bool long_line = !s.whole_lines();
             if (long_line) pl.axis_pingpong = true;
-            if (s.kind == STEP_LINE || s.kind == STEP_PAIR || long_line) pl.generic_pingpong = true;
+            if (s.kind != STEP_AXIS || long_line) pl.generic_pingpong = true;
         }
         if (pl.generic_pingpong) pl.ws_natural = (size_t)pl.N * pl.esize;
     }
@@ -529,8 +579,8 @@ fftu_status run_steps(Plan *pl, const std::vector<Step> &steps, const void *firs
             a.src = src;
             a.dst = dst;
             e = launch_axis_pass(a, is_double, pl->dir, st);
-        } else if (s.kind == STEP_LINE || s.kind == STEP_PAIR) {
-            record_error("internal: a line or pair pass outside the alternating phase-A schedule");
+        } else if (s.kind == STEP_LINE || s.kind == STEP_PAIR || s.kind == STEP_TRIPLE) {
+            record_error("internal: a register-resident pass outside the alternating phase-A schedule");
             return FFTU_ERR_INTERNAL;
         } else if (s.kind == STEP_PHASE_A3) {
             Phase3Launch l = s.a3;
@@ -592,8 +642,8 @@ fftu_status plan_view(fftu_handle h, PlanView *v) {
         sv.is_axis = true;
         sv.axis = s.axis;
         v->a_passes.push_back(sv);
-        if (s.kind == STEP_PAIR) {  // the pair's first axis, in its strided-pass form
-            sv.axis = s.axis2;
+        for (int i = 1; i < s.passes(); ++i) {  // the step's other axes, in their strided-pass form
+            sv.axis = s.strided(i);
             v->a_passes.push_back(sv);
         }
     }
@@ -819,6 +869,7 @@ fftu_status fftu_plan_ex(int d, const int64_t *n, const int64_t *p, fftu_dtype d
     if (e == cudaSuccess) e = prepare_phase_b3(dtype == FFTU_C128, dir);
     if (e == cudaSuccess && dtype == FFTU_C64) e = prepare_line_pass(dir);
     if (e == cudaSuccess && dtype == FFTU_C64) e = prepare_pair_pass(dir);
+    if (e == cudaSuccess && dtype == FFTU_C64) e = prepare_triple_pass(dir);
     if (e != cudaSuccess) {
         free_plan(pl);
         return cuda_fail(e, "kernel attributes");
@@ -876,23 +927,25 @@ fftu_status exec_natural(Plan *pl, fftu_phase phase, const void *in, void *out, 
         for (int k = 1; k <= np; ++k) {
             const Step &s = pl->phase_a[k - 1];
             void *dst = ((np - k) % 2 == 0) ? out : pl->workspace;
-            const bool whole_lines = s.axis.Gt == s.axis.G && (s.kind != STEP_PAIR || s.axis2.Gt == s.axis2.G);
+            const bool whole_lines = s.whole_lines();
             if (dst == src && !(k == 1 && whole_lines && src == out)) {
                 set_err("in-place transform with a long-line axis needs in != out");
                 return FFTU_ERR_UNSUPPORTED;
             }
             cudaError_t e;
-            if (dst == src) {  // the in-place first pass: strided form, then the alternation continues
-                AxisPass a = s.axis;
-                a.src = src;
-                a.dst = out;
-                e = launch_axis_pass(a, pl->dtype == FFTU_C128, pl->dir, st);
-                if (e == cudaSuccess && s.kind == STEP_PAIR) {
-                    a = s.axis2;
+            if (dst == src) {  // the in-place first step: its strided passes, then the alternation continues
+                e = cudaSuccess;
+                for (int i = 0; i < s.passes() && e == cudaSuccess; ++i) {
+                    AxisPass a = s.strided(i);
                     a.src = out;
                     a.dst = out;
                     e = launch_axis_pass(a, pl->dtype == FFTU_C128, pl->dir, st);
                 }
+            } else if (s.kind == STEP_TRIPLE) {
+                TriplePass a = s.triple;
+                a.src = src;
+                a.dst = dst;
+                e = launch_triple_pass(a, pl->dir, st);
             } else if (s.kind == STEP_PAIR) {
                 PairPass a = s.pair;
                 a.src = src;

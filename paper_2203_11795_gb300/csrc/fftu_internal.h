@@ -90,6 +90,20 @@ struct PairPass {
     size_t smem;            // W (p_a p_b L^2 + pad) elements
 };
 
+// Phase A of the last three axes a, b, c in one pass (complex64; see triple_pass.cu), for sub-FFT length 8 on
+// each and p_b p_c = 16.  Same result as three AxisPass of mode 0 (axes c, b, a), never in place.  The array
+// is viewed as [outer][n_a][n_b][n_c]; a CTA of 512 threads takes one outer position and one s_a.
+struct TriplePass {
+    const void *src;
+    void *dst;
+    const void *twa, *twb, *twc;  // w_{n_a}^e, w_{n_b}^e, w_{n_c}^e (forward roots)
+    int64_t outer;
+    int na, nb, nc, pa, pb, pc;
+    int lg_pa, lg_pc;
+    int64_t ctas;                 // outer p_a
+    size_t smem;                  // 8192 elements
+};
+
 // Phase B on the d-dim groups {m + s' (n/p)} with every p_l <= 16, in one pass.
 // Tile = all p values for Mt consecutive m along the last axis.
 struct PhaseBFused {
@@ -184,6 +198,8 @@ cudaError_t launch_pointwise(void *out, const void *mul, int64_t n, int is_doubl
 cudaError_t launch_axis_pass(const AxisPass &a, int is_double, int dir, cudaStream_t st);
 cudaError_t prepare_line_pass(int dir);
 cudaError_t prepare_pair_pass(int dir);
+cudaError_t prepare_triple_pass(int dir);
+cudaError_t launch_triple_pass(const TriplePass &a, int dir, cudaStream_t st);
 cudaError_t launch_pair_pass(const PairPass &a, int dir, cudaStream_t st);
 cudaError_t launch_line_pass(const LinePass &a, int dir, cudaStream_t st);
 // tw1 (len entries), tw2 (len / 16 entries) and twp (nl entries) of a line pass, generated in FP64 and

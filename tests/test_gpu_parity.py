@@ -294,6 +294,52 @@ def test_pair_pass_phase_a_matches_model(fftu, case):
         assert oracle.rel_l2(wa, w_ref) <= tolerance(dt, x.size)
 
 
+# ---- three-axis passes (phase A of the last three axes with 8-point sub-FFTs, p_b p_c = 16) -----------
+
+TRIPLE_CASES = [
+    ((32, 32, 32), (4, 4, 4), np.complex64),              # one triple step only
+    ((2, 32, 32, 32), (1, 4, 4, 4), np.complex64),        # triple, then one axis
+    ((64, 16, 64), (8, 2, 8), np.complex64),              # p_b x p_c = 2 x 8
+    ((16, 16, 64), (2, 2, 8), np.complex64),              # p_a = 2
+    ((2, 32, 32, 32, 32), (1, 4, 4, 4, 4), np.complex64),  # triple and two axes (three steps)
+    ((32, 32, 32, 32, 8), (4, 4, 4, 2, 1), np.complex64),  # no triple (p_c = 1): pairs and axes
+]
+
+
+@pytest.mark.parametrize("case", TRIPLE_CASES, ids=_id)
+@pytest.mark.parametrize("inverse", [False, True])
+@pytest.mark.parametrize("inplace", [False, True])
+def test_triple_passes_match_oracle(fftu, case, inverse, inplace):
+    """Plans whose phase A runs the last three axes in one pass (triple_pass.cu), forward and inverse, in and
+    out of place (in place with an odd number of steps runs the first one as its strided passes), against
+    the oracle; out of place leaves the input untouched."""
+    import torch
+    shape, p, dt = case
+    x = complex_uniform(6161 + len(shape), shape, dtype=dt)
+    t = torch.from_numpy(x).cuda()
+    with fftu.Plan(shape, p, dtype=t.dtype, inverse=inverse) as plan:
+        out = t if inplace else torch.empty_like(t)
+        plan.exec(t, out)
+        torch.cuda.synchronize()
+        plan.check_device_status()
+        y = out.cpu().numpy()
+        if not inplace:
+            assert np.array_equal(t.cpu().numpy(), x)
+    ref = oracle.fftn(x.astype(np.complex128), inverse=inverse)
+    assert oracle.rel_l2(y, ref) <= tolerance(dt, x.size)
+
+
+@pytest.mark.parametrize("case", TRIPLE_CASES[:4], ids=_id)
+def test_triple_pass_phase_a_matches_model(fftu, case):
+    """Phase A alone through a three-axis pass = Supersteps 0 + 1 of the CPU model of Algorithm 2.3."""
+    shape, p, dt = case
+    x = complex_uniform(6262, shape, dtype=dt)
+    for inverse in (False, True):
+        wa, _ = run_gpu(fftu, x, p, inverse=inverse, phase=fftu.FFTU_PHASE_A)
+        w_ref = cm.phase_a(x.astype(np.complex128), p, inverse=inverse)
+        assert oracle.rel_l2(wa, w_ref) <= tolerance(dt, x.size)
+
+
 @pytest.mark.parametrize("p", [(128, 128), (8, 8)], ids=["p128", "p8"])
 def test_full_size_2d_16384(fftu, p):
     """The 2D 16384 x 16384 complex64 workload against the full FP64 oracle."""
