@@ -120,6 +120,9 @@ struct PhaseBFused {
     int64_t tiles;
     int threads;
     double scale;
+    // shared slot of tile element e: e ^ (((e >> swz_src) & swz_mask) << swz_dst) (swz_mask = 0: e itself);
+    // spreads the first DFT pass's runs of Mt < 16 elements over all banks
+    int swz_src, swz_mask, swz_dst;
 };
 
 // Fused 3D phase A (complex64): see phase_a3.cu.

@@ -255,8 +255,15 @@ __device__ __forceinline__ void axis_tile(const AxisPass &a, int64_t t, C *sm, c
     __syncthreads();
 }
 
-template <typename C, int DIR, int R>
-__device__ __forceinline__ void axis_dft(C *sm, int total, int S, int tid, int nt) {
+// Shared slot of phase-B tile element e (see PhaseBFused::swz_*; keeps the pairs (2k, 2k + 1) together).
+// SWZ = false: the identity (no index arithmetic).
+template <bool SWZ> __device__ __forceinline__ int pbs(const PhaseBFused &b, int e) {
+    if constexpr (SWZ) return e ^ (((e >> b.swz_src) & b.swz_mask) << b.swz_dst);
+    else return e;
+}
+
+template <typename C, int DIR, int R, bool SWZ = false>
+__device__ __forceinline__ void axis_dft(const PhaseBFused &pb, C *sm, int total, int S, int tid, int nt) {
     // groups: total / R, group g -> base (g / S) * S * R + g % S, stride S (S a power of two)
     const int groups = total / R;
     const int lg_s = 31 - __clz(S);
@@ -264,24 +271,24 @@ __device__ __forceinline__ void axis_dft(C *sm, int total, int S, int tid, int n
         const int base = ((g >> lg_s) << lg_s) * R + (g & (S - 1));
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = sm[base + r * S];
+        for (int r = 0; r < R; ++r) v[r] = sm[pbs<SWZ>(pb, base + r * S)];
         dft_small<R, DIR>(v);
 #pragma unroll
-        for (int r = 0; r < R; ++r) sm[base + r * S] = v[r];
+        for (int r = 0; r < R; ++r) sm[pbs<SWZ>(pb, base + r * S)] = v[r];
     }
 }
 
 // F_{R1} along a stride-S axis and F_{R2} along the next (stride S R1) in one shared-memory pass: each group
 // holds the R1 x R2 values of one fixed position of the other axes in registers.
-template <typename C, int DIR, int R1, int R2>
-__device__ __forceinline__ void axis_dft2(C *sm, int total, int S, int tid, int nt) {
+template <typename C, int DIR, int R1, int R2, bool SWZ = false>
+__device__ __forceinline__ void axis_dft2(const PhaseBFused &pb, C *sm, int total, int S, int tid, int nt) {
     const int groups = total / (R1 * R2);
     const int lg_s = 31 - __clz(S);
     for (int g = tid; g < groups; g += nt) {
         const int base = ((g >> lg_s) << lg_s) * (R1 * R2) + (g & (S - 1));
         C v[R1 * R2];
 #pragma unroll
-        for (int r = 0; r < R1 * R2; ++r) v[r] = sm[base + r * S];
+        for (int r = 0; r < R1 * R2; ++r) v[r] = sm[pbs<SWZ>(pb, base + r * S)];
 #pragma unroll
         for (int r2 = 0; r2 < R2; ++r2) {
             C w[R1];
@@ -301,7 +308,7 @@ __device__ __forceinline__ void axis_dft2(C *sm, int total, int S, int tid, int 
             for (int r2 = 0; r2 < R2; ++r2) v[r2 * R1 + r1] = w[r2];
         }
 #pragma unroll
-        for (int r = 0; r < R1 * R2; ++r) sm[base + r * S] = v[r];
+        for (int r = 0; r < R1 * R2; ++r) sm[pbs<SWZ>(pb, base + r * S)] = v[r];
     }
 }
 
@@ -335,7 +342,7 @@ __device__ __forceinline__ int64_t phaseb_base(const PhaseBFused &b, int64_t t) 
 
 // The DFT stages of a landed phase-B tile: F_{p_l} along every axis, last axis first, two adjacent axes per
 // shared-memory pass where p_l p_{l-1} <= 16.
-template <typename C, int DIR>
+template <typename C, int DIR, bool SWZ = false>
 __device__ __forceinline__ void phaseb_dfts(const PhaseBFused &b, C *sm) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int total = b.P * b.Mt;
@@ -344,22 +351,22 @@ __device__ __forceinline__ void phaseb_dfts(const PhaseBFused &b, C *sm) {
         const int pp = (l > 0 && b.p[l] > 1 && b.p[l - 1] > 1) ? b.p[l] * b.p[l - 1] : 0;
         if (pp > 0 && pp <= 16) {
             switch (b.p[l] * 100 + b.p[l - 1]) {
-                case 202: axis_dft2<C, DIR, 2, 2>(sm, total, S, tid, nt); break;
-                case 204: axis_dft2<C, DIR, 2, 4>(sm, total, S, tid, nt); break;
-                case 208: axis_dft2<C, DIR, 2, 8>(sm, total, S, tid, nt); break;
-                case 402: axis_dft2<C, DIR, 4, 2>(sm, total, S, tid, nt); break;
-                case 404: axis_dft2<C, DIR, 4, 4>(sm, total, S, tid, nt); break;
-                case 802: axis_dft2<C, DIR, 8, 2>(sm, total, S, tid, nt); break;
+                case 202: axis_dft2<C, DIR, 2, 2, SWZ>(b, sm, total, S, tid, nt); break;
+                case 204: axis_dft2<C, DIR, 2, 4, SWZ>(b, sm, total, S, tid, nt); break;
+                case 208: axis_dft2<C, DIR, 2, 8, SWZ>(b, sm, total, S, tid, nt); break;
+                case 402: axis_dft2<C, DIR, 4, 2, SWZ>(b, sm, total, S, tid, nt); break;
+                case 404: axis_dft2<C, DIR, 4, 4, SWZ>(b, sm, total, S, tid, nt); break;
+                case 802: axis_dft2<C, DIR, 8, 2, SWZ>(b, sm, total, S, tid, nt); break;
                 default: break;
             }
             S *= pp;
             --l;
         } else {
             switch (b.p[l]) {
-                case 2: axis_dft<C, DIR, 2>(sm, total, S, tid, nt); break;
-                case 4: axis_dft<C, DIR, 4>(sm, total, S, tid, nt); break;
-                case 8: axis_dft<C, DIR, 8>(sm, total, S, tid, nt); break;
-                case 16: axis_dft<C, DIR, 16>(sm, total, S, tid, nt); break;
+                case 2: axis_dft<C, DIR, 2, SWZ>(b, sm, total, S, tid, nt); break;
+                case 4: axis_dft<C, DIR, 4, SWZ>(b, sm, total, S, tid, nt); break;
+                case 8: axis_dft<C, DIR, 8, SWZ>(b, sm, total, S, tid, nt); break;
+                case 16: axis_dft<C, DIR, 16, SWZ>(b, sm, total, S, tid, nt); break;
                 default: break;
             }
             S *= b.p[l];
@@ -370,7 +377,7 @@ __device__ __forceinline__ void phaseb_dfts(const PhaseBFused &b, C *sm) {
 
 // One complex64 phase-B tile with the thread's element offsets from the tile base precomputed (16-byte
 // pairs; K pairs per thread at most): the per-element index arithmetic is one add.
-template <int DIR, int K>
+template <int DIR, int K, bool SWZ = false>
 __device__ __forceinline__ void phaseb_tile_pairs(const PhaseBFused &b, int64_t t, float2 *sm, float2 *__restrict__ data,
                                                   const int (&off)[K]) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -380,17 +387,17 @@ __device__ __forceinline__ void phaseb_tile_pairs(const PhaseBFused &b, int64_t 
     for (int k = 0; k < K; ++k) {
         const int e = 2 * (tid + k * nt);
         if (e < total)
-            async_copy_pair(sm + e, data + base + off[k]);
+            async_copy_pair(sm + pbs<SWZ>(b, e), data + base + off[k]);
     }
     async_copy_wait();
     __syncthreads();
-    phaseb_dfts<float2, DIR>(b, sm);
+    phaseb_dfts<float2, DIR, SWZ>(b, sm);
     const float scale = (float)b.scale;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const int e = 2 * (tid + k * nt);
         if (e < total) {
-            float4 v = *reinterpret_cast<const float4 *>(sm + e);
+            float4 v = *reinterpret_cast<const float4 *>(sm + pbs<SWZ>(b, e));
             if (b.scale != 1.0) {
                 v.x *= scale;
                 v.y *= scale;
@@ -404,7 +411,7 @@ __device__ __forceinline__ void phaseb_tile_pairs(const PhaseBFused &b, int64_t 
 }
 
 // One tile of the generic fused phase B (see PhaseBFused): all p values for Mt consecutive m_d.
-template <typename C, int DIR>
+template <typename C, int DIR, bool SWZ = false>
 __device__ __forceinline__ void phaseb_tile(const PhaseBFused &b, int64_t t, C *sm, C *__restrict__ data) {
     using Rl = typename real_of<C>::type;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -425,13 +432,13 @@ __device__ __forceinline__ void phaseb_tile(const PhaseBFused &b, int64_t t, C *
             g += (int64_t)sl * b.L[l] * b.stride[l];
         }
         if (pairs)
-            async_copy_pair(reinterpret_cast<float2 *>(sm + e), reinterpret_cast<const float2 *>(data + g));
+            async_copy_pair(reinterpret_cast<float2 *>(sm + pbs<SWZ>(b, e)), reinterpret_cast<const float2 *>(data + g));
         else
-            async_copy(sm + e, data + g);
+            async_copy(sm + pbs<SWZ>(b, e), data + g);
     }
     async_copy_wait();
     __syncthreads();
-    phaseb_dfts<C, DIR>(b, sm);
+    phaseb_dfts<C, DIR, SWZ>(b, sm);
     const Rl scale = (Rl)b.scale;
     for (int e = tid * step; e < total; e += nt * step) {
         const int mt = e & (b.Mt - 1);
@@ -442,10 +449,10 @@ __device__ __forceinline__ void phaseb_tile(const PhaseBFused &b, int64_t t, C *
             sf >>= b.lg_p[l];
             g += (int64_t)sl * b.L[l] * b.stride[l];
         }
-        C v = sm[e];
+        C v = sm[pbs<SWZ>(b, e)];
         if (b.scale != 1.0) v = cscale(v, scale);
         if (pairs) {
-            C w = sm[e + 1];
+            C w = sm[pbs<SWZ>(b, e + 1)];
             if (b.scale != 1.0) w = cscale(w, scale);
             *reinterpret_cast<float4 *>(data + g) = make_float4(v.x, v.y, w.x, w.y);
         } else {

@@ -25,7 +25,9 @@ namespace {
 constexpr int kPairsPerThread = 16;  // complex64 tiles up to 16 x 2 x 256 elements take the offset path
 
 // complex64: three CTAs of 256 threads per SM (64 KB tiles), the offsets of a thread held in 16 registers.
-template <typename C, int DIR>
+// SWZ: the tile's shared slots are swizzled (PhaseBFused::swz_*); a separate instantiation, so that the
+// other plans run without the index arithmetic.
+template <typename C, int DIR, bool SWZ>
 __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 3 : 1) phase_b_fused_kernel(const __grid_constant__ PhaseBFused b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
@@ -42,25 +44,32 @@ __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 3 : 1) phase_b_fused_ker
                 off[k] = e < b.P * b.Mt ? (int)phaseb_offset(b, e) : 0;
             }
             for (int64_t t = blockIdx.x; t < b.tiles; t += gridDim.x)
-                phaseb_tile_pairs<DIR, kPairsPerThread>(b, t, sm, data, off);
+                phaseb_tile_pairs<DIR, kPairsPerThread, SWZ>(b, t, sm, data, off);
             return;
         }
     }
-    for (int64_t t = blockIdx.x; t < b.tiles; t += gridDim.x) phaseb_tile<C, DIR>(b, t, sm, data);
+    for (int64_t t = blockIdx.x; t < b.tiles; t += gridDim.x) phaseb_tile<C, DIR, SWZ>(b, t, sm, data);
 }
 
 template <typename C, int DIR>
 cudaError_t launch_b_t(const PhaseBFused &b, cudaStream_t st) {
     size_t smem = (size_t)b.P * b.Mt * sizeof(C);
     int64_t grid = b.tiles < (int64_t)1 << 30 ? b.tiles : (int64_t)1 << 30;
-    phase_b_fused_kernel<C, DIR><<<(unsigned)grid, b.threads, smem, st>>>(b);
+    if (sizeof(C) == 8 && b.swz_mask != 0)
+        phase_b_fused_kernel<C, DIR, true><<<(unsigned)grid, b.threads, smem, st>>>(b);
+    else
+        phase_b_fused_kernel<C, DIR, false><<<(unsigned)grid, b.threads, smem, st>>>(b);
     return cudaGetLastError();
 }
 
 template <typename C, int DIR>
 cudaError_t prepare_b_t() {
-    return cudaFuncSetAttribute(phase_b_fused_kernel<C, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kMaxDynSmem);
+    cudaError_t e = cudaFuncSetAttribute(phase_b_fused_kernel<C, DIR, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(phase_b_fused_kernel<C, DIR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kMaxDynSmem);
+    return e;
 }
 
 }  // namespace
