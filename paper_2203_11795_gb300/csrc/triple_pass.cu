@@ -9,7 +9,8 @@
 //
 // A CTA takes one outer position and one s_a: the 8 planes m_a p_a + s_a (8 n_b n_c elements, 64 KB at
 // n_b n_c = 1024) in, the 8 planes s_a 8 + k_a out.  Its 1024 fibers per stage (16 classes x 64) go to 512
-// threads, two each:
+// threads, two each, one after the other (40 registers: three CTAs per SM; both at once took 63 registers, two
+// CTAs per SM, and measured 3% slower):
 //   stage 1: fiber (s_c, s_b, m_b, m_a) loads 8 values along c, F_8, times w_{n_c}^{s_c k_c};
 //   stage 2: fiber (k_c, s_c, s_b, m_a), in place in shared memory: F_8 along b, times w_{n_b}^{s_b k_b};
 //   stage 3: fiber (k_c, s_c, s_b, k_b): F_8 along a, times w_{n_a}^{s_a k_a}, stored at its Put positions
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(kTripleThreads) triple_pass_kernel(const __gri
     float2 v[8];
 
     // stage 1: fiber (s_c, s_b, m_b, m_a) along c
-#pragma unroll
+#pragma unroll 1
     for (int h = 0; h < 2; ++h) {
         const int f = threadIdx.x + h * kTripleThreads;
         const int sc = f & (a.pc - 1), sb = (f >> a.lg_pc) & (a.pb - 1), mb = (f >> 4) & 7, ma = f >> 7;
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(kTripleThreads) triple_pass_kernel(const __gri
     __syncthreads();
 
     // stage 2: fiber (k_c, s_c, s_b, m_a) along b, in place
-#pragma unroll
+#pragma unroll 1
     for (int h = 0; h < 2; ++h) {
         const int f = threadIdx.x + h * kTripleThreads;
         const int kc = f & 7, sc = (f >> 3) & (a.pc - 1), sb = (f >> (3 + a.lg_pc)) & (a.pb - 1), ma = f >> 7;
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(kTripleThreads) triple_pass_kernel(const __gri
     __syncthreads();
 
     // stage 3: fiber (k_c, s_c, s_b, k_b) along a, then the Put store
-#pragma unroll
+#pragma unroll 1
     for (int h = 0; h < 2; ++h) {
         const int f = threadIdx.x + h * kTripleThreads;
         const int kc = f & 7, sc = (f >> 3) & (a.pc - 1), sb = (f >> (3 + a.lg_pc)) & (a.pb - 1), kb = f >> 7;
