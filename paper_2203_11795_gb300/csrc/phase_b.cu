@@ -9,14 +9,21 @@
 // pass is in place.
 //
 // A tile holds all p values for Mt consecutive m_d (the contiguous axis), so
-// every global access is a run of Mt elements.  The DFT along axis l is one
-// radix-p_l butterfly per group, in shared memory; axes are separated by block
-// barriers.  The inverse multiplies by 1/N in the store.
+// every global access is a run of Mt elements.  Two forms of the DFT stages:
+// complex64 runs them in registers (phase_b_reg.cuh: each stage takes one
+// group of at most 16 values per thread, the first loading from HBM and the
+// last storing to it, shared memory in between); complex128, and complex64
+// plans whose first pass is one axis over short runs, run one radix-p_l
+// butterfly per group in a shared tile (generic_tiles.cuh).  Stages are
+// separated by block barriers.  The inverse multiplies by 1/N in the store.
 #include <cuda_runtime.h>
 
 #include "fft_device.cuh"
 #include "fftu_internal.h"
+#include <cstring>
+
 #include "generic_tiles.cuh"
+#include "phase_b_reg.cuh"
 
 namespace fftu {
 
@@ -51,8 +58,79 @@ __global__ void __launch_bounds__(256, sizeof(C) == 8 ? 3 : 1) phase_b_fused_ker
     for (int64_t t = blockIdx.x; t < b.tiles; t += gridDim.x) phaseb_tile<C, DIR, SWZ>(b, t, sm, data);
 }
 
+template <int DIR>
+__global__ void __launch_bounds__(256) phase_b_reg_kernel(const __grid_constant__ PhaseBFused b,
+                                                          const __grid_constant__ PBGroups g) {
+    extern __shared__ __align__(16) float2 pbr_sm[];
+    float2 *__restrict__ data = static_cast<float2 *>(b.data);
+    const float scale = (float)b.scale;
+    for (int64_t t = blockIdx.x; t < b.tiles; t += gridDim.x) {
+        const int64_t base = phaseb_base(b, t);
+        for (int gi = 0; gi < g.n; ++gi) {
+            const bool first = gi == 0, last = gi == g.n - 1;
+            switch (g.lo[gi] * 100 + g.hi[gi]) {
+                case 201: pb_stage<DIR, 2, 1>(b, g, gi, base, pbr_sm, data, first, last, scale); break;
+                case 401: pb_stage<DIR, 4, 1>(b, g, gi, base, pbr_sm, data, first, last, scale); break;
+                case 801: pb_stage<DIR, 8, 1>(b, g, gi, base, pbr_sm, data, first, last, scale); break;
+                case 1601: pb_stage<DIR, 16, 1>(b, g, gi, base, pbr_sm, data, first, last, scale); break;
+                case 202: pb_stage<DIR, 2, 2>(b, g, gi, base, pbr_sm, data, first, last, scale); break;
+                case 204: pb_stage<DIR, 2, 4>(b, g, gi, base, pbr_sm, data, first, last, scale); break;
+                case 402: pb_stage<DIR, 4, 2>(b, g, gi, base, pbr_sm, data, first, last, scale); break;
+                case 404: pb_stage<DIR, 4, 4>(b, g, gi, base, pbr_sm, data, first, last, scale); break;
+                case 208: pb_stage<DIR, 2, 8>(b, g, gi, base, pbr_sm, data, first, last, scale); break;
+                case 802: pb_stage<DIR, 8, 2>(b, g, gi, base, pbr_sm, data, first, last, scale); break;
+                default: break;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Axis groups of the register-resident phase B (the same grouping as phaseb_dfts); false if some axis has
+// p_l > 16 or p_l = 1 between grouped axes is not representable.
+bool pb_groups(const PhaseBFused &b, PBGroups &g) {
+    std::memset(&g, 0, sizeof(g));
+    int off = b.lg_Mt;
+    for (int l = b.d - 1; l >= 0;) {
+        if (b.p[l] == 1) {
+            --l;
+            continue;
+        }
+        const int pp = (l > 0 && b.p[l - 1] > 1) ? b.p[l] * b.p[l - 1] : 0;
+        if (g.n >= FFTU_MAX_DIMS) return false;
+        g.off[g.n] = off;
+        g.lo[g.n] = b.p[l];
+        g.lst_lo[g.n] = b.L[l] * b.stride[l];
+        if (pp > 0 && pp <= 16) {
+            g.hi[g.n] = b.p[l - 1];
+            g.lst_hi[g.n] = b.L[l - 1] * b.stride[l - 1];
+            off += b.lg_p[l] + b.lg_p[l - 1];
+            l -= 2;
+        } else {
+            g.hi[g.n] = 1;
+            g.lst_hi[g.n] = 0;
+            off += b.lg_p[l];
+            l -= 1;
+        }
+        ++g.n;
+    }
+    return g.n > 0;
+}
+
 template <typename C, int DIR>
 cudaError_t launch_b_t(const PhaseBFused &b, cudaStream_t st) {
+    if constexpr (sizeof(C) == 8) {
+        // complex64: the register-resident stages, except where the swizzled shared tile applies (a single-axis
+        // first pass over short runs), which measured faster there (64^4 at p = 8^4: 0.111 against 0.119 ms;
+        // 32^5 at p = 4^5: 0.153 -> 0.134 ms and 16384^2 at p = 16^2: 0.830 -> 0.731 ms with the stages)
+        PBGroups g;
+        if (b.swz_mask == 0 && b.P * b.Mt <= 8192 && pb_groups(b, g)) {
+            const size_t smem = (size_t)b.P * b.Mt * sizeof(C);
+            int64_t grid = b.tiles < (int64_t)1 << 30 ? b.tiles : (int64_t)1 << 30;
+            phase_b_reg_kernel<DIR><<<(unsigned)grid, 256, smem, st>>>(b, g);
+            return cudaGetLastError();
+        }
+    }
     size_t smem = (size_t)b.P * b.Mt * sizeof(C);
     int64_t grid = b.tiles < (int64_t)1 << 30 ? b.tiles : (int64_t)1 << 30;
     if (sizeof(C) == 8 && b.swz_mask != 0)
@@ -64,6 +142,11 @@ cudaError_t launch_b_t(const PhaseBFused &b, cudaStream_t st) {
 
 template <typename C, int DIR>
 cudaError_t prepare_b_t() {
+    if constexpr (sizeof(C) == 8) {
+        cudaError_t e0 = cudaFuncSetAttribute(phase_b_reg_kernel<DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              kMaxDynSmem);
+        if (e0 != cudaSuccess) return e0;
+    }
     cudaError_t e = cudaFuncSetAttribute(phase_b_fused_kernel<C, DIR, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     if (e == cudaSuccess)
